@@ -1,0 +1,40 @@
+/*
+ * ORACLE — test infrastructure only (see gfc_oracle.c). Its own definitions;
+ * it shares no header, type or helper with the product library.
+ */
+#ifndef GFC_ORACLE_H
+#define GFC_ORACLE_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum { ORC_OK = 0, ORC_EINVAL = -1, ORC_ENOMEM = -2 };
+enum { ORC_PROP_SCALAR = 0, ORC_PROP_CPAIR = 1, ORC_PROP_DRESSED = 2 };
+
+typedef struct {
+    int kind;
+    double m2;                  /* SCALAR: 1/(s + m2) on both legs            */
+    double mk2_re, mk2_im;      /* CPAIR: k-leg 1/(s + Mk2) as printed        */
+    double mq2_re, mq2_im;      /* CPAIR: (p-k)-leg 1/(s + Mq2), Mq2 = conj   */
+    double a, b, c;             /* DRESSED: (s + a)/(s^2 + b s + c), b^2 < 4c */
+} orc_prop;
+
+typedef struct {
+    int dim;                    /* 3 or 4                                     */
+    double mu2;                 /* subtraction point, real >= 0               */
+    int n_radial, n_angular;    /* GL orders; n_radial % 4 == 0, n_angular even */
+    double radial_scale;        /* L in |q| = L t/(1-t)                       */
+    double detour_radius;       /* r of the half circle around a swept pole   */
+} orc_params;
+
+int orc_gauss_legendre(int n, double *x, double *w);
+/* x, G interleaved complex128 (re, im); kappa optional (may be NULL). */
+int orc_eval_points(const orc_prop *P, const orc_params *Q, const double *x, long npts,
+                    double *G, double *kappa, int nthreads);
+int orc_grid_points(double re0, double re1, double im0, double im1, int m, int n, double *x);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

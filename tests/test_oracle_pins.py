@@ -1,0 +1,278 @@
+"""Pins of the oracle against what the paper and the mathematics fix.
+
+The oracle (oracle/) is a plain FP64 evaluation of the paper's quadrature.
+These tests check it against values that do not come from it: the paper's
+closed form eq. 18 (golden file), textbook bubble closed forms, exact analytic
+continuations of the Feynman-parameter form, invariants (Schwarz reflection,
+G(mu2) = 0, reality on the spacelike axis, the threshold at -4 m^2), cut-off
+independence (Sect. 2, Step 2) and a library Gauss-Legendre rule. A last test
+compiles the oracle with planted mistakes and shows that each one fails a pin.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from closed_forms import G_exact, dressed_poles
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+GOLD = os.path.join(HERE, "golden")
+PI = np.pi
+
+with open(os.path.join(GOLD, "paper_example.json")) as f:
+    PAPER = json.load(f)
+PAPER_PROP = {"kind": "cpair", "mk2": complex(*PAPER["mk2"]), "mq2": complex(*PAPER["mq2"])}
+
+
+def _eq18_golden():
+    rows = np.loadtxt(os.path.join(GOLD, "eq18_values.txt"))
+    x = rows[:, 2] + 1j * rows[:, 3]
+    g = rows[:, 4] + 1j * rows[:, 5]
+    return rows[:, :2].astype(int), x, g
+
+
+def _dist_to_cut(x, threshold):
+    """distance from x to the half-line (-inf, threshold] of the real axis"""
+    x = np.asarray(x)
+    return np.where(x.real <= threshold, np.abs(x.imag), np.abs(x - threshold))
+
+
+# bulk points of the 64 x 64 bubble rectangle [-8,4] x [-4,4], all quadrants,
+# at least 0.5 away from the real axis where Re x < 0
+BULK = np.array([2 + 1j, 1 - 3j, -1 + 1j, -1 + 3j, -3 + 1j, -3 + 3j, -3 - 3j, -0.5 + 4j,
+                 0.3 + 0.2j, -6 - 2j, -7.5 + 3.5j, 3.9 - 3.9j, -5 + 0.7j, 0.1 - 0.05j])
+
+
+def test_gauss_legendre_matches_library_rule():
+    for n in (1, 2, 3, 7, 64, 256, 2048):
+        x, w = oracle.gauss_legendre(n)
+        xr, wr = np.polynomial.legendre.leggauss(n)
+        assert np.max(np.abs(x - xr)) < 1e-14
+        # numpy's own end weights lose accuracy as n grows (~1e-11 at 256,
+        # ~1e-7 at 2048), so compare with it only up to n = 256
+        if n <= 256:
+            assert np.max(np.abs(w - wr) / wr) < 5e-11
+        # exact for polynomials of degree < 2n: sum w x^k = 2/(k+1), k even
+        for k in range(0, min(2 * n, 40), 2):
+            assert abs(np.sum(w * x ** k) - 2.0 / (k + 1)) < 1e-13
+
+
+def test_grid_is_the_papers_cell_centred_grid():
+    ij, xg, _ = _eq18_golden()
+    g = PAPER["grid"]
+    X = oracle.grid_points(g["re0"], g["re1"], g["im0"], g["im1"], g["m"], g["n"])
+    assert X.shape == (g["m"] * g["n"],)
+    assert np.array_equal(X[ij[:, 0] * g["n"] + ij[:, 1]], xg)
+    # no grid point on the real axis
+    assert np.min(np.abs(X.imag)) > 0
+
+
+def test_paper_worked_example_matches_eq18():
+    """Sect. 5: the detoured contours and the leg relabelling reproduce eq. 18."""
+    _, x, g18 = _eq18_golden()
+    par = dict(dim=4, mu2=0.0, n_radial=1024, n_angular=128)
+    G = oracle.eval_points(PAPER_PROP, par, x)
+    err = np.abs(16 * PI ** 2 * G - g18) / np.abs(g18)
+    d = _dist_to_cut(x, PAPER["threshold"])
+    bulk = d > 0.2
+    assert bulk.sum() >= 15
+    assert np.max(err[bulk]) < 1e-11, err[bulk]
+    # next to the cut the quadrature converges slowly, but it converges
+    assert np.max(err[~bulk]) < 2e-2
+
+
+def test_paper_example_at_the_papers_node_counts():
+    """ngl = 64 per sub-contour suffices in well-behaved areas (Sect. 4):
+    n_radial = 4 * 64 gives 64 nodes on each detour piece."""
+    _, x, g18 = _eq18_golden()
+    par = dict(dim=4, mu2=0.0, n_radial=4 * PAPER["ngl"], n_angular=64)
+    G = oracle.eval_points(PAPER_PROP, par, x)
+    err = np.abs(16 * PI ** 2 * G - g18) / np.abs(g18)
+    bulk = _dist_to_cut(x, PAPER["threshold"]) > 1.0
+    assert np.max(err[bulk]) < 1e-4
+
+
+@pytest.mark.parametrize("dim", [4, 3])
+@pytest.mark.parametrize("m2", [0.25, 1.0, 4.0])
+def test_scalar_bubble_closed_form(dim, m2):
+    prop = {"kind": "scalar", "m2": m2}
+    par = dict(dim=dim, mu2=1.0, n_radial=2048, n_angular=256)
+    # 0.2 rad or more away from the negative real axis, where the angular
+    # integrand nearly pinches and the quadrature converges slowly
+    xs = BULK[np.pi - np.abs(np.angle(BULK)) > 0.2]
+    G = oracle.eval_points(prop, par, xs)
+    ref = np.array([G_exact(prop, x, dim, 1.0) for x in xs])
+    err = np.abs(G - ref) / np.maximum(np.abs(ref), 1e-3 * np.max(np.abs(ref)))
+    assert np.max(err) < 1e-10, err
+
+
+@pytest.mark.parametrize("dim", [4, 3])
+@pytest.mark.parametrize("abc", [(1.0, 0.5, 2.0), (1.3, 0.0, 2.5), (0.7, 0.9, 1.2)])
+def test_dressed_closed_form(dim, abc):
+    a, b, c = abc
+    prop = {"kind": "dressed", "a": a, "b": b, "c": c}
+    (yp, _), _ = dressed_poles(a, b, c)
+    # stay 10 degrees away from the rays arg x = +-arg y+, where the k-leg pole
+    # grazes the radial path and the quadrature converges slowly
+    keep = np.abs(np.abs(np.angle(BULK)) - np.angle(yp)) > np.radians(10)
+    xs = BULK[keep]
+    par = dict(dim=dim, mu2=1.0, n_radial=2048, n_angular=256)
+    G = oracle.eval_points(prop, par, xs)
+    ref = np.array([G_exact(prop, x, dim, 1.0) for x in xs])
+    err = np.abs(G - ref) / np.abs(ref)
+    assert np.max(err) < 1e-10, err
+
+
+@pytest.mark.parametrize("prop", [
+    {"kind": "scalar", "m2": 1.0},
+    PAPER_PROP,
+    {"kind": "dressed", "a": 1.0, "b": 0.5, "c": 2.0},
+])
+@pytest.mark.parametrize("dim", [3, 4])
+def test_schwarz_reflection(prop, dim):
+    """G(conj x) = conj G(x); for the conjugate-pair legs the two half-planes
+    use different leg assignments and detours, so this is not automatic."""
+    xs = np.array([2 + 1j, -1 + 1j, -3 + 3j, -0.5 + 4j, -6 + 2j, 0.3 + 0.1j])
+    par = dict(dim=dim, mu2=1.0, n_radial=512, n_angular=64)
+    G = oracle.eval_points(prop, par, np.concatenate([xs, np.conj(xs)]))
+    n = xs.size
+    assert np.max(np.abs(G[n:] - np.conj(G[:n])) / np.abs(G[:n])) < 1e-13
+
+
+def test_subtraction_point_and_spacelike_axis():
+    prop = {"kind": "scalar", "m2": 1.0}
+    par = dict(dim=4, mu2=1.0, n_radial=512, n_angular=64)
+    G = oracle.eval_points(prop, par, np.array([1.0 + 0j, 0.5, 3.0, 7.0]))
+    assert G[0] == 0
+    # real on the spacelike axis x > 0
+    assert np.max(np.abs(G.imag)) < 1e-17
+    assert np.all(np.abs(G[1:].real) > 1e-5)
+    # the paper example is real on (-1, inf) too, in particular at x > 0
+    G2 = oracle.eval_points(PAPER_PROP, dict(dim=4, mu2=0.0, n_radial=512, n_angular=64),
+                            np.array([0.5 + 0j, 2.0, 4.0]))
+    assert np.max(np.abs(G2.imag)) < 1e-17
+
+
+def test_branch_cut_opens_at_threshold():
+    """16 pi^2 Im G(x + i0) = -pi sqrt(1 + 4 m^2/x) below x = -4 m^2 and 0
+    above it (D = 4, real mass); checked 0.05 off the axis, where the
+    quadrature with 4096 x 2048 nodes has converged, so the limits hold up to
+    O(0.05)."""
+    prop = {"kind": "scalar", "m2": 1.0}
+    par = dict(dim=4, mu2=1.0, n_radial=4096, n_angular=2048)
+    d = 0.05
+    xs = np.array([-2.0, -3.0, -5.0, -6.0]) + 1j * d
+    G = 16 * PI ** 2 * oracle.eval_points(prop, par, np.concatenate([xs, np.conj(xs)]))
+    above, below = G[:4], G[4:]
+    assert np.max(np.abs(above[:2].imag)) < 0.05
+    lim = -PI * np.sqrt(1 + 4 / xs[2:].real)
+    assert np.max(np.abs(above[2:].imag - lim)) < 0.05
+    assert np.max(np.abs(below[2:].imag + lim)) < 0.05
+
+
+def test_cutoff_independence():
+    """The subtracted integral does not depend on where the radial path is cut
+    (Sect. 2, Step 2): changing the scale L of |q| = L t/(1-t) changes nothing."""
+    prop = {"kind": "dressed", "a": 0.7, "b": 0.9, "c": 1.2}
+    xs = np.array([2 + 1j, -3 + 1j, -2 - 1j])
+    res = []
+    for L in (0.5, 1.0, 2.0):
+        res.append(oracle.eval_points(prop, dict(dim=4, mu2=1.0, n_radial=1024, n_angular=128,
+                                                 radial_scale=L), xs))
+    assert np.max(np.abs(res[0] - res[1]) / np.abs(res[1])) < 1e-11
+    assert np.max(np.abs(res[2] - res[1]) / np.abs(res[1])) < 1e-11
+
+
+def test_convergence_under_refinement():
+    prop = {"kind": "scalar", "m2": 1.0}
+    x = np.array([-2 + 0.5j])
+    ref = G_exact(prop, x[0], 4, 1.0)
+    errs = [abs(oracle.eval_points(prop, dict(dim=4, mu2=1.0, n_radial=nr, n_angular=na), x)[0]
+                - ref) for nr, na in ((128, 32), (512, 128), (2048, 256))]
+    assert errs[0] > errs[1] > errs[2]
+    assert errs[2] < 1e-5 * abs(ref)
+
+
+def test_condition_number_reported():
+    """kappa = sum|terms|/|sum| grows as x approaches the negative real axis,
+    where the angular integrand nearly pinches."""
+    prop = {"kind": "scalar", "m2": 1.0}
+    xs = np.array([2 + 1j, -2 + 0.1j, -2 + 0.02j])
+    G, kap = oracle.eval_points(prop, dict(dim=4, mu2=1.0, n_radial=2048, n_angular=256),
+                                xs, with_kappa=True)
+    assert 1.0 <= kap[0] < 10 < kap[1] < kap[2]
+
+
+@pytest.mark.parametrize("bad", [
+    dict(dim=5), dict(n_angular=63), dict(n_radial=250), dict(radial_scale=0.0),
+])
+def test_rejects_bad_parameters(bad):
+    par = dict(dim=4, mu2=1.0, n_radial=256, n_angular=64)
+    par.update(bad)
+    with pytest.raises(ValueError):
+        oracle.eval_points({"kind": "scalar", "m2": 1.0}, par, np.array([1 + 1j]))
+
+
+def test_rejects_bad_inputs():
+    par = dict(dim=4, mu2=1.0, n_radial=256, n_angular=64)
+    with pytest.raises(ValueError):   # on the cut side of the real axis
+        oracle.eval_points({"kind": "scalar", "m2": 1.0}, par, np.array([-2 + 0j]))
+    with pytest.raises(ValueError):   # b^2 >= 4c: no conjugate poles
+        oracle.eval_points({"kind": "dressed", "a": 1, "b": 3, "c": 2}, par, np.array([1 + 1j]))
+    with pytest.raises(ValueError):   # legs not a conjugate pair
+        oracle.eval_points({"kind": "cpair", "mk2": 0.5j, "mq2": 0.4j}, par, np.array([1 + 1j]))
+
+
+# --- planted mistakes -------------------------------------------------------
+
+def _paper_err(orc):
+    _, x, g18 = _eq18_golden()
+    keep = _dist_to_cut(x, PAPER["threshold"]) > 0.2
+    G = orc.eval_points(PAPER_PROP, dict(dim=4, mu2=0.0, n_radial=512, n_angular=64), x[keep])
+    return np.max(np.abs(16 * PI ** 2 * G - g18[keep]) / np.abs(g18[keep]))
+
+
+def _closed_err(orc, prop, dim):
+    (yp, _), _ = dressed_poles(1.0, 0.5, 2.0)
+    keep = (np.abs(np.abs(np.angle(BULK)) - np.angle(yp)) > np.radians(10)) & \
+        (np.pi - np.abs(np.angle(BULK)) > 0.2)
+    xs = BULK[keep]
+    G = orc.eval_points(prop, dict(dim=dim, mu2=1.0, n_radial=1024, n_angular=128), xs)
+    ref = np.array([G_exact(prop, x, dim, 1.0) for x in xs])
+    return np.max(np.abs(G - ref) / np.abs(ref))
+
+
+def _grid_err(orc):
+    ij, xg, _ = _eq18_golden()
+    g = PAPER["grid"]
+    X = orc.grid_points(g["re0"], g["re1"], g["im0"], g["im1"], g["m"], g["n"])
+    return np.max(np.abs(X[ij[:, 0] * g["n"] + ij[:, 1]] - xg))
+
+
+DRESSED = {"kind": "dressed", "a": 1.0, "b": 0.5, "c": 2.0}
+SCALAR = {"kind": "scalar", "m2": 1.0}
+MUTANT_PINS = {
+    1: lambda o: _paper_err(o),
+    2: lambda o: _paper_err(o),
+    3: lambda o: _closed_err(o, DRESSED, 3),
+    4: lambda o: _closed_err(o, SCALAR, 4),
+    5: lambda o: _closed_err(o, SCALAR, 3),
+    6: lambda o: _closed_err(o, SCALAR, 4),
+    7: lambda o: _closed_err(o, DRESSED, 4),
+    8: lambda o: _grid_err(o),
+    9: lambda o: _paper_err(o),
+    10: lambda o: _closed_err(o, DRESSED, 4),
+}
+
+
+@pytest.mark.parametrize("n", sorted(MUTANT_PINS))
+def test_planted_mistake_fails_a_pin(n, tmp_path):
+    pin = MUTANT_PINS[n]
+    # the oracle as written passes the pin at this resolution ...
+    good = pin(oracle.Oracle(oracle._load()))
+    assert good < 1e-4
+    # ... and the oracle with mistake n compiled in fails it
+    bad = pin(oracle.mutant(n, str(tmp_path)))
+    assert not (bad < 1e-2), f"mutant {n} passed its pin (err {bad})"
