@@ -1,0 +1,217 @@
+/*
+ * gfc.h — C ABI of the GB300 library that evaluates Taylor-subtracted
+ * two-point correlators on grids of complex external momentum p^2 = x.
+ *
+ * The operation (Windisch, Alkofer, Haase, Liebmann, arXiv:1205.0752):
+ *
+ *   G(x) = G0(x) - G0(mu2),
+ *   G0(x) = K_D int_C dy (1/2) y^((D-2)/2) int_0^pi dpsi sin^(D-2) psi
+ *              P1(y) [ P2(x + y - 2 sqrt(x y) cos psi) - P2(y) ]
+ *
+ * Sect. 2 Step 1 (eqs. 5-11: hyperspherical reduction, K_D = S_(D-2)/(2 pi)^D),
+ * Step 2 (eqs. 12-14, 20: BPHZ subtraction (1 - t^0) at x = 0), Step 3 (eq. 15:
+ * radial contour C deformed around the poles and the angular cut, Sect. 5.3),
+ * Steps 4-5 (Sect. 4, Kernels 1 and 2: a homogeneous M x N grid of x and one
+ * 2-D Gauss-Legendre quadrature per point). The physical normalisation is
+ * int d^Dq / (2 pi)^D; 16 pi^2 G is the paper's rescaled eq. 18 for its
+ * worked example.
+ *
+ * Conventions for every call:
+ *  - the return value is a status: GFC_OK (0) or a negative GFC_E* code;
+ *    gfc_last_error() gives a thread-local message for the last failure;
+ *  - no C++ exception crosses this boundary;
+ *  - complex arrays are interleaved complex128: element k is (re, im) at
+ *    [2k, 2k+1], 16-byte aligned;
+ *  - "device" pointers are CUDA global-memory pointers on the current device;
+ *    the caller owns them and keeps them alive until the work on `stream`
+ *    (a cudaStream_t passed as void*; NULL = the legacy default stream) has
+ *    finished; the calls return once the work is enqueued;
+ *  - on an invalid argument nothing is enqueued and no output is written;
+ *  - the library owns its node tables and scratch (device memory it
+ *    allocates on first use per device and keeps until gfc_release()).
+ */
+#ifndef GFC_H
+#define GFC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GFC_VERSION_MAJOR 1
+#define GFC_VERSION_MINOR 0
+
+enum {
+    GFC_OK = 0,
+    GFC_EINVAL = -1,     /* an argument is out of range; nothing was done      */
+    GFC_ENOMEM = -2,     /* device or host allocation failed                   */
+    GFC_EBUDGET = -3,    /* a request does not fit the server's memory budget   */
+    GFC_ECUDA = -4,      /* a CUDA runtime call failed (message has the name)  */
+    GFC_ETIMEOUT = -5,   /* a wait ran out of time                             */
+    GFC_ECANCELED = -6,  /* the request was cancelled                          */
+    GFC_EBUSY = -7,      /* the server is shutting down or the queue is full   */
+    GFC_ENOTFOUND = -8   /* unknown ticket                                     */
+};
+
+/* Propagator on both legs (Sect. 5, eq. 16; the dressed form is the
+ * propagator family of the correlators studied in ref. [aw3] of the paper). */
+typedef enum {
+    GFC_PROP_SCALAR = 0,   /* 1/(s + m2), m2 > 0 real, on both legs            */
+    GFC_PROP_CPAIR = 1,    /* k-leg 1/(s + Mk2), (p-k)-leg 1/(s + Mq2),
+                              Mq2 = conj(Mk2), Im Mk2 != 0; the paper's example
+                              is Mk2 = +i/2, Mq2 = -i/2 (eq. 19)               */
+    GFC_PROP_DRESSED = 2   /* (s + a)/(s^2 + b s + c) on both legs, b^2 < 4c   */
+} gfc_prop_kind;
+
+typedef struct {
+    int kind;                   /* gfc_prop_kind                               */
+    double m2;                  /* SCALAR                                      */
+    double mk2_re, mk2_im;      /* CPAIR                                       */
+    double mq2_re, mq2_im;      /* CPAIR                                       */
+    double a, b, c;             /* DRESSED                                     */
+} gfc_propagator;
+
+typedef enum {
+    GFC_FP64 = 0,    /* every step in IEEE binary64                            */
+    GFC_MIXED = 1    /* angular sums and per-node set-up in binary32 with
+                        compensated binary32 radial sums; binary64 for the
+                        epilogue and for every point in the binary64 band     */
+} gfc_precision;
+
+typedef struct {
+    int dim;               /* 3 or 4                                           */
+    double mu2;            /* subtraction point, real, >= 0; G(mu2) = 0        */
+    int n_radial;          /* Gauss-Legendre order on the radial half-line;
+                              multiple of 4, 4 <= n_radial <= 16384            */
+    int n_angular;         /* Gauss-Legendre order in psi on [0, pi]; even,
+                              2 <= n_angular <= 512                            */
+    double radial_scale;   /* L in |q| = L t/(1-t); > 0                        */
+    double detour_radius;  /* r of the half circle around a k-leg pole; > 0 and
+                              below half the pole's modulus (paper: 0.1)       */
+    int precision;         /* gfc_precision                                    */
+    double cut_band;       /* MIXED: points closer than this to a branch cut
+                              half-line are evaluated in binary64 (0.05)       */
+    double pinch_angle;    /* MIXED: points whose radial ray lies within this
+                              angle (radians) of a leg's pinch direction are
+                              evaluated in binary64 (default 0: off)           */
+    double mixed_rtol;     /* MIXED: a point whose binary32 sum has an
+                              estimated rounding error above mixed_rtol |G| is
+                              evaluated again in binary64 (default 1e-6;
+                              0 turns this off, leaving the cut band only)     */
+} gfc_params;
+
+/* Cell-centred grid of Kernel 1 (Sect. 4): x_ij = re0 + (i + 1/2)(re1-re0)/m
+ * + i (im0 + (j + 1/2)(im1-im0)/n), i < m along Re x, j < n along Im x,
+ * stored at flat index i*n + j. */
+typedef struct {
+    double re0, re1, im0, im1;
+    int m, n;
+} gfc_grid;
+
+/* Per-call counters of the last evaluation on this thread. */
+typedef struct {
+    int64_t points;            /* points of the call                           */
+    int64_t points_fp64;       /* MIXED: points evaluated in binary64 (cut band
+                                  and a-posteriori routing); FP64: all          */
+    int64_t node_evals;        /* sum over evaluated points of contour nodes x
+                                  angular nodes (all passes; binary32 and
+                                  binary64 evaluations both counted)            */
+    int kernel_launches;       /* kernels enqueued by the call                  */
+} gfc_eval_stats;
+
+const char *gfc_strerror(int status);
+/* Thread-local text of the last failure on this thread ("" if none). */
+const char *gfc_last_error(void);
+int gfc_version(int *major, int *minor);
+
+/* Defaults: D = 4, mu2 = 1, 2048 x 256 nodes, L = 1, r = 0.1, FP64,
+ * cut_band 0.05, pinch_angle 0, mixed_rtol 1e-6. */
+int gfc_params_default(gfc_params *p);
+
+/* Steps 4-5 on caller-given points: x and G are DEVICE arrays of npts
+ * complex128. A point on the negative real axis (Im x = 0, Re x < 0) lies on
+ * the cut side where the method is undefined; its G is written as NaN.
+ * npts = 0 is valid and enqueues nothing. */
+int gfc_eval_points(const gfc_propagator *prop, const gfc_params *params,
+                    const double *x, int64_t npts, double *G, void *stream);
+
+/* As gfc_eval_points, and if `cond` is not NULL it receives, per point, the
+ * scale K_D sum_k M_k of the magnitudes of the node contributions (DEVICE
+ * array of npts doubles): the rounding error of a point is a small multiple
+ * of the unit roundoff of its precision times this number. */
+int gfc_eval_points_cond(const gfc_propagator *prop, const gfc_params *params,
+                         const double *x, int64_t npts, double *G, double *cond, void *stream);
+
+/* Steps 4-5 on the cell-centred grid (Kernel 1 fused into Kernel 2): G is a
+ * DEVICE array of m*n complex128, G[i*n + j]. GFC_EINVAL if a grid row lies
+ * on the negative real axis. */
+int gfc_eval_grid(const gfc_propagator *prop, const gfc_params *params,
+                  const gfc_grid *grid, double *G, void *stream);
+
+/* Kernel 1 alone (Step 4): writes the m*n grid points to the DEVICE array x. */
+int gfc_grid_points(const gfc_grid *grid, double *x, void *stream);
+
+/* End-to-end form of gfc_eval_points for HOST arrays (pageable or pinned):
+ * copies x to the device, evaluates, copies G back and waits for the stream;
+ * uses library-owned device buffers. */
+int gfc_eval_points_host(const gfc_propagator *prop, const gfc_params *params,
+                         const double *x_host, int64_t npts, double *G_host, void *stream);
+
+/* Counters of the last gfc_eval_* call made on this thread; waits for the
+ * work of that call to finish (the counts are read from the device). */
+int gfc_last_stats(gfc_eval_stats *out);
+
+/* Frees the library-owned device memory of the current device (node tables,
+ * scratch, staging buffers). Must not overlap any work still running. */
+int gfc_release(void);
+
+/* ------------------------------------------------------------------------ */
+/* Serving: continuous batching of grid requests into persistent launches.   */
+/* ------------------------------------------------------------------------ */
+
+typedef struct gfc_server gfc_server;
+
+typedef struct {
+    uint64_t submitted, completed, rejected, canceled;
+    double p50_ms, p99_ms;          /* submit -> completion latency           */
+    double points_per_s;            /* completed points / wall time since create */
+    int64_t points_done;
+    size_t bytes_in_use, bytes_budget;
+    int64_t launches;               /* batched launches so far                */
+    int queued, active;             /* requests waiting / on the device       */
+} gfc_stats;
+
+/* One server per device; `hbm_budget_bytes` bounds the device memory the
+ * server holds for admitted requests (output grids and staging); at most
+ * `max_slots` requests are on the device at once. */
+int gfc_server_create(int device, size_t hbm_budget_bytes, int max_slots, gfc_server **out);
+
+/* Queues one grid request and returns at once with a ticket. G_host receives
+ * m*n complex128 values (host memory that stays valid until the request
+ * completes or is cancelled). GFC_EBUDGET if the request alone exceeds the
+ * budget, GFC_EINVAL on a bad argument, GFC_EBUSY when shutting down. */
+int gfc_server_submit(gfc_server *s, const gfc_propagator *prop, const gfc_params *params,
+                      const gfc_grid *grid, double *G_host, uint64_t *ticket);
+
+/* done = 1 once the request finished; status then holds its result code. */
+int gfc_server_poll(gfc_server *s, uint64_t ticket, int *done, int *status);
+
+/* Waits up to timeout_ms (< 0: without limit) for the request; returns its
+ * status, or GFC_ETIMEOUT if it is still running when the time is up. */
+int gfc_server_wait(gfc_server *s, uint64_t ticket, int timeout_ms);
+
+/* Cancels a request that has not finished; its G_host is not written after
+ * this returns GFC_OK. */
+int gfc_server_cancel(gfc_server *s, uint64_t ticket);
+
+int gfc_server_stats(gfc_server *s, gfc_stats *out);
+
+/* Cancels what is still queued, drains what is on the device, frees all. */
+int gfc_server_destroy(gfc_server *s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GFC_H */

@@ -40,7 +40,7 @@ class _Params(ctypes.Structure):
 
 def _compile(out: str, defines=()) -> None:
     tmp = out + f".{os.getpid()}.tmp"
-    subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", *defines, "-o", tmp,
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared", *defines, "-o", tmp,
                            _SRC, "-lm", "-lpthread"])
     os.replace(tmp, out)
 

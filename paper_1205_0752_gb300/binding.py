@@ -1,0 +1,358 @@
+"""ctypes binding of libgfc (include/gfc.h): argument marshalling only.
+
+Every evaluation runs in the library's CUDA kernels. PyTorch provides device
+memory and streams. If the shared library cannot be built or loaded, every
+call raises; there is no CPU path.
+"""
+from __future__ import annotations
+
+import ctypes
+import threading
+from dataclasses import dataclass
+
+from . import build as _build
+
+GFC_OK, GFC_EINVAL, GFC_ENOMEM, GFC_EBUDGET, GFC_ECUDA = 0, -1, -2, -3, -4
+GFC_ETIMEOUT, GFC_ECANCELED, GFC_EBUSY, GFC_ENOTFOUND = -5, -6, -7, -8
+GFC_PROP_SCALAR, GFC_PROP_CPAIR, GFC_PROP_DRESSED = 0, 1, 2
+GFC_FP64, GFC_MIXED = 0, 1
+
+
+class GfcError(RuntimeError):
+    def __init__(self, status: int, where: str, detail: str):
+        super().__init__(f"{where}: status {status} ({detail})")
+        self.status = status
+
+
+class _Prop(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("m2", ctypes.c_double),
+                ("mk2_re", ctypes.c_double), ("mk2_im", ctypes.c_double),
+                ("mq2_re", ctypes.c_double), ("mq2_im", ctypes.c_double),
+                ("a", ctypes.c_double), ("b", ctypes.c_double), ("c", ctypes.c_double)]
+
+
+class _Params(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("mu2", ctypes.c_double),
+                ("n_radial", ctypes.c_int), ("n_angular", ctypes.c_int),
+                ("radial_scale", ctypes.c_double), ("detour_radius", ctypes.c_double),
+                ("precision", ctypes.c_int), ("cut_band", ctypes.c_double),
+                ("pinch_angle", ctypes.c_double), ("mixed_rtol", ctypes.c_double)]
+
+
+class _Grid(ctypes.Structure):
+    _fields_ = [("re0", ctypes.c_double), ("re1", ctypes.c_double),
+                ("im0", ctypes.c_double), ("im1", ctypes.c_double),
+                ("m", ctypes.c_int), ("n", ctypes.c_int)]
+
+
+class _EvalStats(ctypes.Structure):
+    _fields_ = [("points", ctypes.c_int64), ("points_fp64", ctypes.c_int64),
+                ("node_evals", ctypes.c_int64), ("kernel_launches", ctypes.c_int)]
+
+
+class _ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64),
+                ("rejected", ctypes.c_uint64), ("canceled", ctypes.c_uint64),
+                ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double),
+                ("points_per_s", ctypes.c_double), ("points_done", ctypes.c_int64),
+                ("bytes_in_use", ctypes.c_size_t), ("bytes_budget", ctypes.c_size_t),
+                ("launches", ctypes.c_int64), ("queued", ctypes.c_int), ("active", ctypes.c_int)]
+
+
+# every symbol of include/gfc.h with (argtypes, restype)
+_P = ctypes.c_void_p
+_SIGS = {
+    "gfc_strerror": ([ctypes.c_int], ctypes.c_char_p),
+    "gfc_last_error": ([], ctypes.c_char_p),
+    "gfc_version": ([ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
+    "gfc_params_default": ([ctypes.POINTER(_Params)], ctypes.c_int),
+    "gfc_eval_points": ([ctypes.POINTER(_Prop), ctypes.POINTER(_Params), _P, ctypes.c_int64, _P,
+                         _P], ctypes.c_int),
+    "gfc_eval_points_cond": ([ctypes.POINTER(_Prop), ctypes.POINTER(_Params), _P, ctypes.c_int64,
+                              _P, _P, _P], ctypes.c_int),
+    "gfc_eval_grid": ([ctypes.POINTER(_Prop), ctypes.POINTER(_Params), ctypes.POINTER(_Grid), _P,
+                       _P], ctypes.c_int),
+    "gfc_grid_points": ([ctypes.POINTER(_Grid), _P, _P], ctypes.c_int),
+    "gfc_eval_points_host": ([ctypes.POINTER(_Prop), ctypes.POINTER(_Params), _P, ctypes.c_int64,
+                              _P, _P], ctypes.c_int),
+    "gfc_last_stats": ([ctypes.POINTER(_EvalStats)], ctypes.c_int),
+    "gfc_release": ([], ctypes.c_int),
+    "gfc_server_create": ([ctypes.c_int, ctypes.c_size_t, ctypes.c_int, ctypes.POINTER(_P)],
+                          ctypes.c_int),
+    "gfc_server_submit": ([_P, ctypes.POINTER(_Prop), ctypes.POINTER(_Params),
+                           ctypes.POINTER(_Grid), _P, ctypes.POINTER(ctypes.c_uint64)],
+                          ctypes.c_int),
+    "gfc_server_poll": ([_P, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int),
+                         ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
+    "gfc_server_wait": ([_P, ctypes.c_uint64, ctypes.c_int], ctypes.c_int),
+    "gfc_server_cancel": ([_P, ctypes.c_uint64], ctypes.c_int),
+    "gfc_server_stats": ([_P, ctypes.POINTER(_ServerStats)], ctypes.c_int),
+    "gfc_server_destroy": ([_P], ctypes.c_int),
+}
+
+_lib = None
+_lock = threading.Lock()
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load_library(build_if_missing: bool = True):
+    """Loads libgfc.so (building it with nvcc if it is missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build() if build_if_missing else _build.LIB
+            lib = ctypes.CDLL(path)
+            for name, (argt, rest) in _SIGS.items():
+                fn = getattr(lib, name)
+                fn.argtypes = argt
+                fn.restype = rest
+            _lib = lib
+    return _lib
+
+
+def _check(status: int, where: str):
+    if status != GFC_OK:
+        lib = load_library()
+        detail = lib.gfc_last_error().decode() or lib.gfc_strerror(status).decode()
+        raise GfcError(status, where, detail)
+
+
+# --------------------------------------------------------------------------
+# argument types
+# --------------------------------------------------------------------------
+
+def make_prop(spec) -> _Prop:
+    """``spec``: {'kind': 'scalar', 'm2': ...} | {'kind': 'cpair', 'mk2': c, 'mq2': c}
+    | {'kind': 'dressed', 'a': .., 'b': .., 'c': ..}"""
+    if isinstance(spec, _Prop):
+        return spec
+    p = _Prop()
+    k = spec["kind"]
+    if k == "scalar":
+        p.kind, p.m2 = GFC_PROP_SCALAR, float(spec["m2"])
+    elif k == "cpair":
+        mk2, mq2 = complex(spec["mk2"]), complex(spec["mq2"])
+        p.kind = GFC_PROP_CPAIR
+        p.mk2_re, p.mk2_im, p.mq2_re, p.mq2_im = mk2.real, mk2.imag, mq2.real, mq2.imag
+    elif k == "dressed":
+        p.kind = GFC_PROP_DRESSED
+        p.a, p.b, p.c = float(spec["a"]), float(spec["b"]), float(spec["c"])
+    else:
+        raise ValueError(f"unknown propagator kind {k!r}")
+    return p
+
+
+def make_params(spec=None, **kw) -> _Params:
+    """Defaults of gfc_params_default, overridden by ``spec``/keywords;
+    ``precision`` may be 'fp64' or 'mixed'."""
+    if isinstance(spec, _Params) and not kw:
+        return spec
+    lib = load_library()
+    q = _Params()
+    _check(lib.gfc_params_default(ctypes.byref(q)), "gfc_params_default")
+    d = dict(spec or {})
+    d.update(kw)
+    for k, v in d.items():
+        if k == "precision":
+            v = {"fp64": GFC_FP64, "mixed": GFC_MIXED}.get(v, v)
+        if not hasattr(q, k):
+            raise ValueError(f"unknown parameter {k!r}")
+        setattr(q, k, type(getattr(q, k))(v))
+    return q
+
+
+def make_grid(re0, re1, im0, im1, m, n) -> _Grid:
+    return _Grid(float(re0), float(re1), float(im0), float(im1), int(m), int(n))
+
+
+def _stream_ptr(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+# --------------------------------------------------------------------------
+# one-shot evaluation
+# --------------------------------------------------------------------------
+
+def eval_points(prop, params, x, out=None, stream=None):
+    """G at the complex128 CUDA tensor ``x`` (any shape); returns a complex128
+    tensor of the same shape, enqueued on ``stream`` (default: current)."""
+    import torch
+    lib = load_library()
+    if x.dtype != torch.complex128 or not x.is_cuda or not x.is_contiguous():
+        raise ValueError("x must be a contiguous complex128 CUDA tensor")
+    G = out if out is not None else torch.empty_like(x)
+    _check(lib.gfc_eval_points(ctypes.byref(make_prop(prop)), ctypes.byref(make_params(params)),
+                               ctypes.c_void_p(x.data_ptr()), x.numel(),
+                               ctypes.c_void_p(G.data_ptr()), _stream_ptr(stream)),
+           "gfc_eval_points")
+    return G
+
+
+def eval_points_cond(prop, params, x, out=None, cond=None, stream=None):
+    """As eval_points, also returning the per-point magnitude scale
+    K_D sum_k M_k (float64 CUDA tensor) of gfc_eval_points_cond."""
+    import torch
+    lib = load_library()
+    if x.dtype != torch.complex128 or not x.is_cuda or not x.is_contiguous():
+        raise ValueError("x must be a contiguous complex128 CUDA tensor")
+    G = out if out is not None else torch.empty_like(x)
+    c = cond if cond is not None else torch.empty(x.shape, dtype=torch.float64, device=x.device)
+    _check(lib.gfc_eval_points_cond(ctypes.byref(make_prop(prop)),
+                                    ctypes.byref(make_params(params)),
+                                    ctypes.c_void_p(x.data_ptr()), x.numel(),
+                                    ctypes.c_void_p(G.data_ptr()), ctypes.c_void_p(c.data_ptr()),
+                                    _stream_ptr(stream)),
+           "gfc_eval_points_cond")
+    return G, c
+
+
+def eval_grid(prop, params, grid, out=None, stream=None, device=None):
+    """G on the cell-centred grid as an (m, n) complex128 CUDA tensor."""
+    import torch
+    lib = load_library()
+    g = grid if isinstance(grid, _Grid) else make_grid(*grid)
+    G = out if out is not None else torch.empty((g.m, g.n), dtype=torch.complex128,
+                                                device=device or "cuda")
+    _check(lib.gfc_eval_grid(ctypes.byref(make_prop(prop)), ctypes.byref(make_params(params)),
+                             ctypes.byref(g), ctypes.c_void_p(G.data_ptr()), _stream_ptr(stream)),
+           "gfc_eval_grid")
+    return G
+
+
+def grid_points(grid, stream=None, device=None):
+    """Kernel 1 alone: the (m, n) grid of x as a complex128 CUDA tensor."""
+    import torch
+    lib = load_library()
+    g = grid if isinstance(grid, _Grid) else make_grid(*grid)
+    x = torch.empty((g.m, g.n), dtype=torch.complex128, device=device or "cuda")
+    _check(lib.gfc_grid_points(ctypes.byref(g), ctypes.c_void_p(x.data_ptr()), _stream_ptr(stream)),
+           "gfc_grid_points")
+    return x
+
+
+def eval_points_host(prop, params, x_host, G_host=None, stream=None):
+    """End-to-end call on host arrays (numpy complex128 or pinned CPU tensors):
+    copy in, evaluate, copy out, wait."""
+    import numpy as np
+    lib = load_library()
+    if isinstance(x_host, np.ndarray):
+        x_host = np.ascontiguousarray(x_host, dtype=np.complex128)
+        G = G_host if G_host is not None else np.empty_like(x_host)
+        xp, gp, n = x_host.ctypes.data, G.ctypes.data, x_host.size
+    else:
+        G = G_host if G_host is not None else x_host.new_empty(x_host.shape)
+        xp, gp, n = x_host.data_ptr(), G.data_ptr(), x_host.numel()
+    _check(lib.gfc_eval_points_host(ctypes.byref(make_prop(prop)),
+                                    ctypes.byref(make_params(params)), ctypes.c_void_p(xp), n,
+                                    ctypes.c_void_p(gp), _stream_ptr(stream)),
+           "gfc_eval_points_host")
+    return G
+
+
+@dataclass
+class EvalStats:
+    points: int
+    points_fp64: int
+    node_evals: int
+    kernel_launches: int
+
+
+def last_stats() -> EvalStats:
+    lib = load_library()
+    s = _EvalStats()
+    _check(lib.gfc_last_stats(ctypes.byref(s)), "gfc_last_stats")
+    return EvalStats(s.points, s.points_fp64, s.node_evals, s.kernel_launches)
+
+
+def version():
+    lib = load_library()
+    a, b = ctypes.c_int(), ctypes.c_int()
+    _check(lib.gfc_version(ctypes.byref(a), ctypes.byref(b)), "gfc_version")
+    return a.value, b.value
+
+
+def release():
+    _check(load_library().gfc_release(), "gfc_release")
+
+
+# --------------------------------------------------------------------------
+# serving
+# --------------------------------------------------------------------------
+
+@dataclass
+class ServerStats:
+    submitted: int
+    completed: int
+    rejected: int
+    canceled: int
+    p50_ms: float
+    p99_ms: float
+    points_per_s: float
+    points_done: int
+    bytes_in_use: int
+    bytes_budget: int
+    launches: int
+    queued: int
+    active: int
+
+
+class Server:
+    """Continuous-batching server on one device (gfc_server_*)."""
+
+    def __init__(self, device: int = 0, hbm_budget_bytes: int = 40 << 30, max_slots: int = 64):
+        self._lib = load_library()
+        h = ctypes.c_void_p()
+        _check(self._lib.gfc_server_create(device, hbm_budget_bytes, max_slots, ctypes.byref(h)),
+               "gfc_server_create")
+        self._h = h
+        self._keep = {}   # ticket -> host buffer kept alive until completion
+
+    def submit(self, prop, params, grid, out=None):
+        """Queues a grid request; returns (ticket, host output array)."""
+        import numpy as np
+        g = grid if isinstance(grid, _Grid) else make_grid(*grid)
+        G = out if out is not None else np.empty((g.m, g.n), dtype=np.complex128)
+        t = ctypes.c_uint64()
+        _check(self._lib.gfc_server_submit(self._h, ctypes.byref(make_prop(prop)),
+                                           ctypes.byref(make_params(params)), ctypes.byref(g),
+                                           ctypes.c_void_p(G.ctypes.data), ctypes.byref(t)),
+               "gfc_server_submit")
+        self._keep[t.value] = G
+        return t.value, G
+
+    def poll(self, ticket):
+        done, st = ctypes.c_int(), ctypes.c_int()
+        _check(self._lib.gfc_server_poll(self._h, ticket, ctypes.byref(done), ctypes.byref(st)),
+               "gfc_server_poll")
+        return bool(done.value), st.value
+
+    def wait(self, ticket, timeout_ms: int = -1) -> int:
+        """Returns the request's status (GFC_ETIMEOUT if still running)."""
+        return self._lib.gfc_server_wait(self._h, ticket, int(timeout_ms))
+
+    def cancel(self, ticket) -> int:
+        return self._lib.gfc_server_cancel(self._h, ticket)
+
+    def stats(self) -> ServerStats:
+        s = _ServerStats()
+        _check(self._lib.gfc_server_stats(self._h, ctypes.byref(s)), "gfc_server_stats")
+        return ServerStats(s.submitted, s.completed, s.rejected, s.canceled, s.p50_ms, s.p99_ms,
+                           s.points_per_s, s.points_done, s.bytes_in_use, s.bytes_budget,
+                           s.launches, s.queued, s.active)
+
+    def close(self):
+        if self._h:
+            _check(self._lib.gfc_server_destroy(self._h), "gfc_server_destroy")
+            self._h = None
+            self._keep.clear()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

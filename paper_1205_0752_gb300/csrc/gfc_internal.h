@@ -1,0 +1,153 @@
+// Internal definitions shared by the host side of libgfc and its kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace gfc {
+
+constexpr int kMaxRadial = 16384;
+constexpr int kMaxAngular = 512;
+constexpr int kMaxPairs = kMaxAngular / 2;
+constexpr int kMaxRules = 16;
+
+// Contour of one pass of a point (Step 3, eq. 15).
+enum PassKind : int { PASS_RAY = 0, PASS_DETOUR = 1 };
+
+// What one launch evaluates.
+enum LaunchMode : int {
+    MODE_ALL = 0,        // every point (FP64 precision)
+    MODE_BULK32 = 1,     // mixed, binary32: every point not in the binary64
+                         // band; band points and points whose estimated
+                         // rounding error exceeds mixed_rtol go to the list
+    MODE_LIST64 = 2      // mixed, binary64: the points of the list
+};
+
+// Per-propagator constants prepared on the host in FP64. Poles y_p are the
+// zeros of the leg denominators in the y = q^2 plane.
+struct PropConst {
+    int kind;            // gfc_prop_kind
+    // SCALAR
+    double m2;
+    // CPAIR after relabelling: yu = pole in the upper half plane, yl = conj(yu);
+    // for Im x > 0 the k-leg carries yu (P1 = 1/(y - yu)) and the (p-k)-leg yl.
+    double yu_re, yu_im;
+    double arg_yu;       // in (0, pi)
+    double yk0_re, yk0_im;   // k-leg pole as given (used on the real axis)
+    // DRESSED: (s + a)/(s^2 + b s + c) = Rp/(s - yp) + Rm/(s - ym), ym = conj(yp)
+    double a, b, c;
+    double yp_re, yp_im, Rp_re, Rp_im;
+    double arg_yp;       // in (0, pi)
+    // binary64 band of the mixed precision
+    double thr;          // branch point on the real axis: the cut is (-inf, thr]
+    double pinch;        // |arg| of the ray direction where the angular
+                         // integrand pinches (pi for real masses), < 0: none
+};
+
+// Kernel parameters (passed by value, __grid_constant__).
+struct KParams {
+    int dim;
+    int n_r;             // radial nodes
+    int n_s;             // nodes per detour segment (n_r / 4)
+    int npair;           // angular pairs (n_angular / 2)
+    int mode;            // LaunchMode
+    int use_grid;        // 1: x from the grid spec, 0: from x[]
+    int64_t npts;
+    // grid (Kernel 1)
+    double re0, dre, im0, dim_im;
+    int gm, gn;
+    const double *x;     // interleaved complex128 (when !use_grid)
+    double *G;           // interleaved complex128 output
+    // node tables (device, FP64 and FP32 copies)
+    const double2 *rad64;   // (rho_k, W_k)
+    const float2 *rad32;
+    const double2 *seg64;   // (t_k, w_k) on [0, 1]
+    const float2 *seg32;
+    const double2 *arc64;   // (cos pi t_k, sin pi t_k)
+    const float2 *arc32;
+    double L, r_detour, K_D, mu2;
+    double Omega, Omega1, delta;     // sum w, sum w t, 4 Omega1 - Omega (pairs)
+    PropConst pc;
+    // mixed-precision routing
+    double cut_band, pinch_angle;
+    double mixed_rtol;           // a-posteriori routing threshold (0: off)
+    int64_t *list;               // points routed to binary64
+    unsigned long long *list_count;
+    double *cond_out;            // optional per-point K_D sum_k M_k
+    // compressed angular rules: Gauss rules of the discrete measure
+    // sum_j e_j delta(t - t_j) with rule_n[r] nodes; rule r reproduces the full
+    // pair sum of 1/(1 - w t) to rounding level when rho(w) >= rho_min{32,64}[r]
+    int nrule;
+    int rule_off[kMaxRules], rule_n[kMaxRules];
+    float rho_min32[kMaxRules], rho_min64[kMaxRules];
+    const double *rules64;   // per node (tau, gamma, gamma tau)
+    const float4 *rules32;   // per node (tau, gamma, gamma tau, 0)
+    int rules_total;         // nodes over all rules
+    // scratch
+    const double *g0mu;  // complex G0(mu2) (2 doubles)
+    unsigned long long *counter;  // work counter for dynamic point assignment
+    unsigned long long *node_count;  // optional: contour nodes x angular nodes
+};
+
+// Angular pair table: t = cos^2 psi_j, e = w t^2, g = w t^3 (w includes the
+// sin^(D-2) psi weight), for the pairs (psi_j, pi - psi_j), j < npair.
+template <typename T, int NP>
+struct AngTab {
+    T t[NP], e[NP], g[NP];
+};
+
+// size of the constant-bank table of a kernel specialised for NP pairs
+// (NP = 0: any number of pairs, table read from shared memory)
+template <int NP>
+constexpr int tab_size() { return NP > 0 ? NP : 1; }
+
+// Host-side launchers (gfc_kernels.cu). Tables: (t, e, g) per pair, FP64.
+struct DevTables {
+    const double *ang64;     // 3 * npair, interleaved (t, e, g)
+    const float *ang32;
+    const double *t, *e, *g; // host copies
+};
+
+// Continuous batching: one work item is a contiguous point range of one
+// request slot.
+struct BatchItem {
+    int slot;
+    int pad;
+    int64_t p0, p1;
+};
+
+struct BatchLaunch {
+    const KParams *slots;        // device array of request descriptors
+    const BatchItem *items;      // device
+    const int64_t *offs;         // device, first launch-wide index of item i
+    int nitems;
+    int64_t total;               // points in the launch
+    unsigned long long *counter; // device, zero before the launch
+    int mode;
+    int npair;
+    int rules_total;             // compressed-rule nodes of the launch's angular rule
+};
+
+cudaError_t launch_batch(const BatchLaunch &bl, const DevTables &tb, bool fp32, bool two_terms,
+                         cudaStream_t st);
+cudaError_t launch_g0mu(const KParams &kp, const DevTables &tb, double mu2, double *partials,
+                        int nwarps, unsigned *ticket, double *g0mu_out,
+                        unsigned long long *counters, cudaStream_t st);
+cudaError_t launch_eval(const KParams &kp, const DevTables &tb, bool fp32, cudaStream_t st);
+cudaError_t launch_grid_points(double re0, double dre, double im0, double dim_im, int m, int n,
+                               double *x, cudaStream_t st);
+
+// ---------------------------------------------------------------------------
+// host side (gfc_capi.cpp), shared with the serving runtime
+// ---------------------------------------------------------------------------
+struct Tables;
+int fail(int code, const char *msg);
+int cuda_fail(cudaError_t e, const char *what);
+int check_params_c(const void *params);
+int check_grid_c(const void *grid);
+int make_prop_c(const void *prop, const void *params, PropConst &pc);
+int get_tables_c(int dev, int n_r, int n_a, int dim, double L, Tables **out, size_t *bytes);
+void fill_kparams_c(KParams &kp, const void *params, const Tables &T, const PropConst &pc);
+DevTables dev_tables_c(const Tables &T);
+
+}  // namespace gfc

@@ -1,0 +1,183 @@
+"""Parity of the CUDA path (through the C ABI) with the oracle.
+
+Element by element on seeded inputs at sizes the oracle finishes in seconds
+(several tiles of 32-lane node slices, ragged tails), and at the full
+production size on seeded samples. Tolerances (relative, with a floor tau =
+1e-3 max|G| that guards the zero at x = mu2): 1e-10 for FP64, 1e-6 for MIXED.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synthetic_inputs as si
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_1205_0752_gb300 as gfc  # noqa: E402
+
+RTOL = {"fp64": 1e-10, "mixed": 1e-6}
+
+
+def rel_err(G, ref, floor_frac=1e-3):
+    G = np.asarray(G).ravel()
+    ref = np.asarray(ref).ravel()
+    tau = floor_frac * np.max(np.abs(ref))
+    return np.abs(G - ref) / np.maximum(np.abs(ref), tau)
+
+
+def assert_parity(G, ref, rtol, x=None, what=""):
+    e = rel_err(G, ref)
+    k = int(np.argmax(e))
+    where = f" at x={np.asarray(x).ravel()[k]}" if x is not None else ""
+    assert e[k] <= rtol, f"{what}: max rel err {e[k]:.3e}{where} (G={np.ravel(G)[k]}, ref={np.ravel(ref)[k]})"
+
+
+def oracle_params(p):
+    return {k: p[k] for k in ("dim", "mu2", "n_radial", "n_angular", "radial_scale",
+                              "detour_radius") if k in p}
+
+
+def run_grid(prop, params, rect, m, n):
+    G = gfc.eval_grid(prop, params, (*rect, m, n))
+    torch.cuda.synchronize()
+    return G.cpu().numpy()
+
+
+SCALAR = {"kind": "scalar", "m2": 1.0}
+PAPER = {"kind": "cpair", "mk2": 0.5j, "mq2": -0.5j}
+
+
+def test_grid_points_bit_exact():
+    for rect, m, n in ((si.grid_rect("small"), 64, 64), (si.grid_rect("paper"), 128, 128),
+                       ((-10.0, 5.0, -5.0, 5.0), 37, 53)):
+        x = gfc.grid_points((*rect, m, n))
+        torch.cuda.synchronize()
+        xo = oracle.grid_points(*rect, m, n)
+        assert np.array_equal(x.cpu().numpy().ravel(), xo)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_bubble_64x64_grid(precision):
+    """The 64 x 64 bubble grid (m = 1, D = 4, mu2 = 1, 256 x 64 nodes)."""
+    rect = si.grid_rect("small")
+    par = dict(dim=4, mu2=1.0, n_radial=256, n_angular=64, precision=precision)
+    G = run_grid(SCALAR, par, rect, 64, 64)
+    x = oracle.grid_points(*rect, 64, 64)
+    ref = oracle.eval_points(SCALAR, oracle_params(par), x)
+    assert_parity(G, ref, RTOL[precision], x, f"bubble 64x64 {precision}")
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_paper_worked_example_grid(precision):
+    """Sect. 5: 128 x 128 over [-5,5]^2, masses -+ i/2, x = 0 subtraction,
+    64 nodes per sub-contour and 64 angular nodes."""
+    rect = si.grid_rect("paper")
+    par = dict(dim=4, mu2=0.0, n_radial=256, n_angular=64, precision=precision)
+    G = run_grid(PAPER, par, rect, 128, 128)
+    x = oracle.grid_points(*rect, 128, 128)
+    ref = oracle.eval_points(PAPER, oracle_params(par), x)
+    assert_parity(G, ref, RTOL[precision], x, f"paper example {precision}")
+
+
+@pytest.mark.parametrize("dim", [3, 4])
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_dressed_grid(dim, precision):
+    """Dressed propagator, a seeded (a, b, c) draw, ragged 48 x 40 grid."""
+    a, b, c = si.dressed_draws(3, 1)[0]
+    prop = {"kind": "dressed", "a": a, "b": b, "c": c}
+    rect = si.grid_rect("small")
+    par = dict(dim=dim, mu2=1.0, n_radial=512, n_angular=64, precision=precision)
+    G = run_grid(prop, par, rect, 48, 40)
+    x = oracle.grid_points(*rect, 48, 40)
+    ref = oracle.eval_points(prop, oracle_params(par), x)
+    assert_parity(G, ref, RTOL[precision], x, f"dressed D={dim} {precision}")
+
+
+@pytest.mark.parametrize("n_angular", [2, 10, 64, 128, 256, 300])
+def test_angular_orders_and_generic_path(n_angular):
+    """Specialised (64, 128, 256) and generic angular orders, FP64."""
+    xs = np.array([2 + 1j, -3 + 1j, -1 - 3j, 0.5 + 0.01j, -7 + 3.5j])
+    par = dict(dim=4, mu2=1.0, n_radial=64, n_angular=n_angular, precision="fp64")
+    G = gfc.eval_points(SCALAR, par, torch.tensor(xs, device="cuda"))
+    torch.cuda.synchronize()
+    ref = oracle.eval_points(SCALAR, oracle_params(par), xs)
+    assert_parity(G.cpu().numpy(), ref, 1e-10, xs, f"n_angular={n_angular}")
+
+
+@pytest.mark.parametrize("npts", [0, 1, 31, 33, 1000])
+def test_ragged_point_counts(npts):
+    g = si.SplitMix64(11)
+    xs = np.array([complex(-8 + 12 * g.uniform(), -4 + 8 * g.uniform()) for _ in range(npts)])
+    par = dict(dim=4, mu2=1.0, n_radial=128, n_angular=64, precision="fp64")
+    xt = torch.tensor(xs, dtype=torch.complex128, device="cuda")
+    G = gfc.eval_points(SCALAR, par, xt)
+    torch.cuda.synchronize()
+    if npts:
+        ref = oracle.eval_points(SCALAR, oracle_params(par), xs)
+        assert_parity(G.cpu().numpy(), ref, 1e-10, xs, f"npts={npts}")
+
+
+def test_edge_points():
+    """x = mu2 gives 0, the positive real axis is real, the negative real axis
+    (cut side, undefined) gives NaN, the smallest contour (n_radial = 4)."""
+    par = dict(dim=4, mu2=1.0, n_radial=4, n_angular=2, precision="fp64")
+    xs = np.array([1.0 + 0j, 3.0 + 0j, -2.0 + 0j, 1e-9 + 1e-9j, 50.0 - 40.0j])
+    G = gfc.eval_points(SCALAR, par, torch.tensor(xs, device="cuda")).cpu().numpy()
+    assert G[0] == 0
+    assert G[1].imag == 0 or abs(G[1].imag) < 1e-18
+    assert np.isnan(G[2].real) and np.isnan(G[2].imag)
+    ref = oracle.eval_points(SCALAR, oracle_params(par), xs[[0, 1, 3, 4]])
+    assert_parity(G[[0, 1, 3, 4]], ref, 1e-10, xs[[0, 1, 3, 4]], "edge points")
+
+
+def test_rejects_bad_arguments():
+    x = torch.tensor([1 + 1j], dtype=torch.complex128, device="cuda")
+    for bad in (dict(dim=5), dict(n_angular=7), dict(n_radial=6), dict(radial_scale=0.0)):
+        with pytest.raises(gfc.GfcError):
+            gfc.eval_points(SCALAR, dict(bad), x)
+    with pytest.raises(gfc.GfcError):
+        gfc.eval_points({"kind": "dressed", "a": 1, "b": 3, "c": 2}, {}, x)
+    with pytest.raises(gfc.GfcError):   # the grid row Im x = 0 with Re x < 0
+        gfc.eval_grid(SCALAR, {}, (-2.0, 1.0, -1.5, 1.5, 4, 3))
+
+
+def test_host_path_matches_device_path():
+    xs = oracle.grid_points(*si.grid_rect("small"), 16, 16)
+    par = dict(dim=4, mu2=1.0, n_radial=256, n_angular=64, precision="fp64")
+    Gd = gfc.eval_points(SCALAR, par, torch.tensor(xs, device="cuda")).cpu().numpy()
+    Gh = gfc.eval_points_host(SCALAR, par, xs)
+    assert np.array_equal(Gd, Gh)
+
+
+def test_row_shards_equal_unsharded():
+    """Weak-scaling layout: disjoint row shards of a grid, evaluated as
+    separate requests, reproduce the whole grid bit for bit."""
+    rect = si.grid_rect("production")
+    m, n = 64, 48
+    par = dict(dim=4, mu2=1.0, n_radial=128, n_angular=64, precision="fp64")
+    whole = run_grid(SCALAR, par, rect, m, n)
+    x = oracle.grid_points(*rect, m, n).reshape(m, n)
+    parts = []
+    for r0, r1 in ((0, 20), (20, 41), (41, 64)):
+        xs = torch.tensor(x[r0:r1].ravel(), device="cuda")
+        parts.append(gfc.eval_points(SCALAR, par, xs).cpu().numpy().reshape(r1 - r0, n))
+    assert np.array_equal(np.concatenate(parts), whole)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("m2", [0.25, 1.0, 4.0])
+def test_production_grid_sampled(precision, m2):
+    """1024 x 1024 over [-10,5] x [-5,5], 2048 x 256 nodes (the launch the
+    benchmark times), checked on a seeded sample of 96 points."""
+    prop = {"kind": "scalar", "m2": m2}
+    rect = si.grid_rect("production")
+    par = dict(dim=4, mu2=1.0, n_radial=2048, n_angular=256, precision=precision)
+    G = run_grid(prop, par, rect, 1024, 1024).ravel()
+    idx = si.sample_indices(2024, 1024 * 1024, 96)
+    x = oracle.grid_points(*rect, 1024, 1024)[idx]
+    ref = oracle.eval_points(prop, oracle_params(par), x)
+    assert_parity(G[idx], ref, RTOL[precision], x, f"production m2={m2} {precision}")
