@@ -97,6 +97,8 @@ __device__ __forceinline__ C<T> csqrt_p(C<T> z)
 
 template <typename T>
 __device__ __forceinline__ T cabs2(C<T> a) { return a.r * a.r + a.i * a.i; }
+template <typename T>
+__device__ __forceinline__ T cabs1(C<T> a) { return fabs(a.r) + fabs(a.i); }
 
 // ----------------------------------------------------------------------------
 // per-point contour plan (Step 3)
@@ -515,6 +517,7 @@ __device__ __forceinline__ C<T> node_value(const KParams &kp, const AngTab<T, ta
     T A[NT], B[NT];
     pair_sums<T, NP, NT>(kp, tab, kp.npair, stab, srules, w, A, B);
     const T Om = T(kp.Omega), Om1 = T(kp.Omega1), del = T(kp.delta);
+    const bool want_mag = sizeof(T) == 4 || kp.cond_out != nullptr;
     C<T> x2 = T(2) * x;
     C<T> sum = {T(0), T(0)};
     mag = T(0);
@@ -526,8 +529,10 @@ __device__ __forceinline__ C<T> node_value(const KParams &kp, const AngTab<T, ta
         C<T> lead = (del * nd.y - Om * (x + tm.m2q)) * ia[s] - Om1 * w[s];
         C<T> vw = (v[s] - w[s]) * w[s];
         C<T> S = lead + vw * T2;
-        // size of S without cancellation between its parts (A, B > 0)
-        T Sabs = tsqrt(cabs2(lead)) + tsqrt(cabs2(vw)) * (A[s] + tsqrt(cabs2(w[s])) * B[s]);
+        // size of S without cancellation between its parts (A, B > 0), in
+        // the |re| + |im| norm (no square roots); only the error estimate of
+        // the binary32 path and the optional cond output use it
+        T Sabs = want_mag ? cabs1(lead) + cabs1(vw) * (A[s] + cabs1(w[s]) * B[s]) : T(0);
         // (1 + |y|) P1(y)
         C<T> p1;
         if (tm.full) {
@@ -541,9 +546,9 @@ __device__ __forceinline__ C<T> node_value(const KParams &kp, const AngTab<T, ta
         C<T> pq = nd.sc * cinv(nd.y + tm.m2q);
         C<T> f = (tm.c * (p1 * pq)) * (x2 * ia[s]);
         sum = sum + f * S;
-        mag += tsqrt(cabs2(f)) * Sabs;
+        if (want_mag) mag += cabs1(f) * Sabs;
     }
-    mag *= tsqrt(cabs2(nd.Jt));
+    if (want_mag) mag *= cabs1(nd.Jt);
     return nd.Jt * sum;
 }
 
