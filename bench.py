@@ -52,9 +52,10 @@ def dist_setup():
     return ws, rank, local
 
 
-def shard_rows(rank: int, world: int, side: int = SIDE):
+def shard_rows(rank: int, world: int, side: int = None):
     """Rows of the (world*side) x side global grid owned by `rank`, and the
     rectangle of that block."""
+    side = SIDE if side is None else side
     re0, re1, im0, im1 = RECT
     total = world * side
     dre = (re1 - re0) / total
@@ -213,15 +214,16 @@ def run_gfc(args):
     torch.cuda.set_device(dev)
     import paper_1205_0752_gb300 as gfc
 
-    rect, _ = shard_rows(rank, ws)
-    grid = gfc.make_grid(*rect, SIDE, SIDE)
+    side = args.side
+    rect, _ = shard_rows(rank, ws, side)
+    grid = gfc.make_grid(*rect, side, side)
     par64 = gfc.make_params(dim=4, mu2=1.0, n_radial=NR, n_angular=NA, precision="fp64")
     parmx = gfc.make_params(dim=4, mu2=1.0, n_radial=NR, n_angular=NA, precision="mixed")
     props = [gfc.make_prop({"kind": "scalar", "m2": m2}) for m2 in MASSES2]
-    outs = [torch.empty((SIDE, SIDE), dtype=torch.complex128, device=dev) for _ in MASSES2]
+    outs = [torch.empty((side, side), dtype=torch.complex128, device=dev) for _ in MASSES2]
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
-    npts_step = 3 * SIDE * SIDE
+    npts_step = 3 * side * side
 
     def barrier():
         if ws > 1:
@@ -278,6 +280,11 @@ def run_gfc(args):
     node_evals_launch = st64.node_evals
     value = ws * npts_step * args.steps / t64
     G64 = [G.clone() for G in outs]
+    if args.quick:
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": ws * npts_step * args.steps / t64,
+                              "unit": "points/s", "quick": True, "side": side}), flush=True)
+        return 0
 
     # ---- mixed precision study --------------------------------------------
     per_launch_mx = []
@@ -297,7 +304,7 @@ def run_gfc(args):
 
     # ---- end to end through the host-buffer C-ABI call --------------------
     import oracle  # grid points of the block, written by the oracle's Kernel 1
-    xh = torch.from_numpy(oracle.grid_points(*rect, SIDE, SIDE)).pin_memory()
+    xh = torch.from_numpy(oracle.grid_points(*rect, side, side)).pin_memory()
     Gh = torch.empty_like(xh).pin_memory()
     for _ in range(1):
         for p in props:
@@ -341,8 +348,8 @@ def run_gfc(args):
                   "error_vs": "FP64 GPU results (parity <= 1e-10 with the oracle)",
                   "fp32_peak_tflops": SM_COUNT * FP32_FMA_PER_SM_CLK * 2 * SM_MAX_MHZ * 1e6 / 1e12,
                   "achieved_tflops": FLOP_PER_NODE_EVAL * 3 * node_evals_launch * args.steps / tmx / 1e12},
-        "e2e": {"value": e2e_value, "unit": "points/s", "h2d_bytes_per_step": 3 * 16 * SIDE * SIDE,
-                "d2h_bytes_per_step": 3 * 16 * SIDE * SIDE},
+        "e2e": {"value": e2e_value, "unit": "points/s", "h2d_bytes_per_step": 3 * 16 * side * side,
+                "d2h_bytes_per_step": 3 * 16 * side * side},
     }
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         v, dt = oracle_points_per_s(args.ref_points)
@@ -366,6 +373,10 @@ def main():
     ap.add_argument("--impl", default="gfc", choices=["gfc", "reference"])
     ap.add_argument("--ref-points", type=int, default=768)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--side", type=int, default=SIDE,
+                    help="grid side per GPU (the benchmark workload is 1024)")
+    ap.add_argument("--quick", action="store_true",
+                    help="FP64 timing only (profiling runs)")
     ap.add_argument("--serve", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=2000)
     ap.add_argument("--serve-rate", type=float, default=200.0)
