@@ -159,6 +159,23 @@ int gfc_grid_points(const gfc_grid *grid, double *x, void *stream);
 int gfc_eval_points_host(const gfc_propagator *prop, const gfc_params *params,
                          const double *x_host, int64_t npts, double *G_host, void *stream);
 
+/* gfc_eval_points (GFC_FP64 only) for callers that cannot allocate device
+ * memory: code that runs while another component owns the device heap, code
+ * that may not call cudaMalloc/cudaFree where it stands (those calls
+ * synchronise the device and are not allowed in every context), or an
+ * embedding with a fixed device-memory plan. The paper has no counterpart.
+ * Its node tables and scratch live in one file-scope device array of about
+ * 150 KB, so the call allocates nothing (no cudaMalloc, cudaFree or
+ * allocating library call); x and G are the caller's DEVICE arrays as for
+ * gfc_eval_points. Limits: precision GFC_FP64, n_radial <= 4096,
+ * n_angular <= 512; larger sizes or GFC_MIXED give GFC_EINVAL. The array is
+ * shared by every call on a device and keeps the last call's contents: calls
+ * that overlap on the GPU (other streams or host threads) race on it. The
+ * first call on a device looks up the array's address with that device
+ * current; make that first call before any stream capture. */
+int gfc_eval_points_noalloc(const gfc_propagator *prop, const gfc_params *params,
+                            const double *x, int64_t npts, double *G, void *stream);
+
 /* Counters of the last gfc_eval_* call made on this thread; waits for the
  * work of that call to finish (the counts are read from the device). */
 int gfc_last_stats(gfc_eval_stats *out);

@@ -72,6 +72,8 @@ _SIGS = {
                               _P, _P, _P], ctypes.c_int),
     "gfc_eval_grid": ([ctypes.POINTER(_Prop), ctypes.POINTER(_Params), ctypes.POINTER(_Grid), _P,
                        _P], ctypes.c_int),
+    "gfc_eval_points_noalloc": ([ctypes.POINTER(_Prop), ctypes.POINTER(_Params), _P,
+                                 ctypes.c_int64, _P, _P], ctypes.c_int),
     "gfc_grid_points": ([ctypes.POINTER(_Grid), _P, _P], ctypes.c_int),
     "gfc_eval_points_host": ([ctypes.POINTER(_Prop), ctypes.POINTER(_Params), _P, ctypes.c_int64,
                               _P, _P], ctypes.c_int),
