@@ -1,0 +1,115 @@
+// Double-binary32 ("double-float") arithmetic: a value is hi + lo with two
+// binary32 numbers, |lo| <= ulp(hi)/2, about 48 significant bits. Built from
+// error-free transformations: Knuth's TwoSum, Dekker's FastTwoSum, and the
+// FMA-based TwoProduct (see Ogita, Rump & Oishi, "Accurate sum and dot
+// product", SIAM J. Sci. Comput. 26 (2005)). On a GB300 the binary32 pipes
+// run 64 times the binary64 FMA rate, so these ~10-20 binary32 operations per
+// double-float operation still outrun native binary64.
+//
+// The exponent range is binary32's (|x| < 3.4e38; the low part underflows
+// below ~1e-38 * 2^-24); the kernels keep every quantity in range by
+// construction (scaled node weights, normalised angular sums).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math.h>
+
+namespace gfc {
+
+// the binary32/binary64 overloads stay visible next to the df ones below
+using ::fabs;
+using ::fma;
+using ::fmin;
+
+struct df {
+    float hi, lo;
+    df() = default;
+    __host__ __device__ constexpr df(float h, float l) : hi(h), lo(l) {}
+    // from a binary64 value: hi = nearest binary32, lo = the rest rounded
+    __host__ __device__ explicit df(double d) : hi((float)d), lo((float)(d - (double)(float)d)) {}
+    __host__ __device__ explicit df(int i) : hi((float)i), lo(0.0f) {}
+    __host__ __device__ explicit operator double() const { return (double)hi + (double)lo; }
+    __host__ __device__ explicit operator float() const { return hi + lo; }
+};
+
+__device__ __forceinline__ df df_two_sum(float a, float b)
+{
+    float s = __fadd_rn(a, b);
+    float bb = __fsub_rn(s, a);
+    float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return df(s, e);
+}
+
+// requires |a| >= |b| (or a = 0)
+__device__ __forceinline__ df df_fast_two_sum(float a, float b)
+{
+    float s = __fadd_rn(a, b);
+    float e = __fsub_rn(b, __fsub_rn(s, a));
+    return df(s, e);
+}
+
+__device__ __forceinline__ df df_two_prod(float a, float b)
+{
+    float p = __fmul_rn(a, b);
+    float e = __fmaf_rn(a, b, -p);
+    return df(p, e);
+}
+
+__device__ __forceinline__ df operator+(df a, df b)
+{
+    df s = df_two_sum(a.hi, b.hi);
+    df t = df_two_sum(a.lo, b.lo);
+    s.lo = __fadd_rn(s.lo, t.hi);
+    s = df_fast_two_sum(s.hi, s.lo);
+    s.lo = __fadd_rn(s.lo, t.lo);
+    return df_fast_two_sum(s.hi, s.lo);
+}
+
+__device__ __forceinline__ df operator-(df a) { return df(-a.hi, -a.lo); }
+__device__ __forceinline__ df operator-(df a, df b) { return a + (-b); }
+
+__device__ __forceinline__ df operator*(df a, df b)
+{
+    df p = df_two_prod(a.hi, b.hi);
+    p.lo = __fmaf_rn(a.hi, b.lo, p.lo);
+    p.lo = __fmaf_rn(a.lo, b.hi, p.lo);
+    return df_fast_two_sum(p.hi, p.lo);
+}
+
+__device__ __forceinline__ df fma(df a, df b, df c) { return a * b + c; }
+
+// 1/a: binary32 seed, then one Newton step r + r (1 - a r) in double-float,
+// which doubles the ~24 correct bits of the seed
+__device__ __forceinline__ df rcp(df a)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(a.hi));
+    df ar = a * df(r, 0.0f);
+    df e = df(1.0f, 0.0f) - ar;
+    return df(r, 0.0f) + df(r, 0.0f) * e;
+}
+
+__device__ __forceinline__ df operator/(df a, df b) { return a * rcp(b); }
+
+// square root: binary32 seed, one Newton step on x = s + (a - s^2)/(2 s)
+__device__ __forceinline__ df tsqrt(df a)
+{
+    if (a.hi <= 0.0f) return df(0.0f, 0.0f);
+    float s = sqrtf(a.hi);
+    df s2 = df_two_prod(s, s);
+    df d = a - s2;
+    float corr = __fdiv_rn(d.hi, 2.0f * s);
+    return df_fast_two_sum(s, corr);
+}
+
+__device__ __forceinline__ df fabs(df a) { return a.hi < 0.0f ? -a : a; }
+__device__ __forceinline__ df fmin(df a, df b) { return (a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo)) ? a : b; }
+__device__ __forceinline__ bool operator<(df a, df b) { return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo); }
+__device__ __forceinline__ bool operator>(df a, df b) { return b < a; }
+__device__ __forceinline__ bool operator>=(df a, df b) { return !(a < b); }
+__device__ __forceinline__ bool operator<=(df a, df b) { return !(b < a); }
+__device__ __forceinline__ bool operator==(df a, df b) { return a.hi == b.hi && a.lo == b.lo; }
+__device__ __forceinline__ df &operator+=(df &a, df b) { a = a + b; return a; }
+__device__ __forceinline__ df &operator*=(df &a, df b) { a = a * b; return a; }
+
+}  // namespace gfc

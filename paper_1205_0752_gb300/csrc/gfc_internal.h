@@ -65,6 +65,8 @@ struct KParams {
     const float2 *seg32;
     const double2 *arc64;   // (cos pi t_k, sin pi t_k)
     const float2 *arc32;
+    // double-float copies: (a.hi, a.lo, b.hi, b.lo) per node
+    const float4 *rad_df, *seg_df, *arc_df;
     double L, r_detour, K_D, mu2;
     double Omega, Omega1, delta;     // sum w, sum w t, 4 Omega1 - Omega (pairs)
     PropConst pc;
@@ -82,6 +84,7 @@ struct KParams {
     float rho_min32[kMaxRules], rho_min64[kMaxRules];
     const double *rules64;   // per node (tau, gamma, gamma tau)
     const float4 *rules32;   // per node (tau, gamma, gamma tau, 0)
+    const float2 *rules_df;  // per node (tau, gamma, gamma tau) as double-float
     int rules_total;         // nodes over all rules
     // scratch
     const double *g0mu;  // complex G0(mu2) (2 doubles)
@@ -105,6 +108,7 @@ constexpr int tab_size() { return NP > 0 ? NP : 1; }
 struct DevTables {
     const double *ang64;     // 3 * npair, interleaved (t, e, g)
     const float *ang32;
+    const float2 *ang_df;    // double-float copy
     const double *t, *e, *g; // host copies
 };
 
@@ -128,12 +132,14 @@ struct BatchLaunch {
     int rules_total;             // compressed-rule nodes of the launch's angular rule
 };
 
-cudaError_t launch_batch(const BatchLaunch &bl, const DevTables &tb, bool fp32, bool two_terms,
+cudaError_t launch_batch(const BatchLaunch &bl, const DevTables &tb, int arith, bool two_terms,
                          cudaStream_t st);
 cudaError_t launch_g0mu(const KParams &kp, const DevTables &tb, double mu2, double *partials,
                         int nwarps, unsigned *ticket, double *g0mu_out,
                         unsigned long long *counters, cudaStream_t st);
-cudaError_t launch_eval(const KParams &kp, const DevTables &tb, bool fp32, cudaStream_t st);
+// arithmetic of a launch
+enum Arith : int { ARITH_F64 = 0, ARITH_F32 = 1, ARITH_DF = 2 };
+cudaError_t launch_eval(const KParams &kp, const DevTables &tb, int arith, cudaStream_t st);
 cudaError_t launch_grid_points(double re0, double dre, double im0, double dim_im, int m, int n,
                                double *x, cudaStream_t st);
 

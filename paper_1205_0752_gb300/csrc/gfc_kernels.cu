@@ -21,9 +21,15 @@
 #include <math.h>
 #include <stdint.h>
 
+#include "gfc_df.h"
 #include "gfc_internal.h"
 
 namespace gfc {
+
+// calibration of the binary32 error estimate (multiple of 2^-24 per unit of
+// the nodes' error scale), from binary32-vs-FP64 runs over the test grids
+constexpr double kMixedErrFactor = 2.0;
+constexpr float kMixedPinchQ = 1e-3f;   // |1 - w t|^2 below which a point is routed
 
 // ----------------------------------------------------------------------------
 // complex arithmetic
@@ -251,6 +257,15 @@ __device__ __forceinline__ void load2<double>(const KParams &kp, int which, int 
 }
 
 template <>
+__device__ __forceinline__ void load2<df>(const KParams &kp, int which, int k, df &a, df &b)
+{
+    const float4 *p = which == 0 ? kp.rad_df : (which == 1 ? kp.seg_df : kp.arc_df);
+    float4 v = __ldg(p + k);
+    a = df(v.x, v.y);
+    b = df(v.z, v.w);
+}
+
+template <>
 __device__ __forceinline__ void load2<float>(const KParams &kp, int which, int k, float &a,
                                              float &b)
 {
@@ -262,7 +277,7 @@ __device__ __forceinline__ void load2<float>(const KParams &kp, int which, int k
 
 // q-ray node: q = (rho0 + rho_k) e^{i theta}, measure q^(D-1) dq
 template <typename T>
-__device__ __forceinline__ Node<T> ray_node(const KParams &kp, int k, C<T> eth, T rho0)
+__device__ __forceinline__ Node<T> ray_node(const KParams &kp, int k, C<T> eth, C<T> eD, T rho0)
 {
     T rho, W;
     load2<T>(kp, 0, k, rho, W);
@@ -274,9 +289,7 @@ __device__ __forceinline__ Node<T> ray_node(const KParams &kp, int k, C<T> eth, 
     n.sc = T(1) + r2;
     T s = rcp(n.sc);
     s = s * s;
-    // q^(D-1) e^{i theta} = rho^(D-1) e^{i D theta}
-    C<T> e2 = eth * eth;
-    C<T> eD = kp.dim == 4 ? e2 * e2 : e2 * eth;
+    // q^(D-1) e^{i theta} = rho^(D-1) e^{i D theta};
     // rho^(D-1) W / (1 + rho^2)^2, scaled first so binary32 cannot overflow
     T rs = r2 * s;
     T mag = (kp.dim == 4 ? rs * rho : rs) * W;
@@ -307,15 +320,15 @@ __device__ __forceinline__ Node<T> finish_y_node(const KParams &kp, C<T> y, C<T>
 // detour node k of 3 n_s + n_r: q-segment 0 -> q1, half circle around yp,
 // straight segment out to R_d e^{i phi}, ray to infinity from |q| = sqrt(R_d)
 template <typename T>
-__device__ __forceinline__ Node<T> detour_node(const KParams &kp, int k, C<T> eth, C<T> yp,
-                                               C<T> x)
+__device__ __forceinline__ Node<T> detour_node(const KParams &kp, int k, C<T> eth, C<T> eD,
+                                               C<T> yp, C<T> x)
 {
     const int ns = kp.n_s;
     T ap = tsqrt(cabs2(yp));
     C<T> u = (rcp(ap)) * yp;
     T r = T(kp.r_detour);
     T Rd = tsqrt(cabs2(x)) + T(20);
-    if (k >= 3 * ns) return ray_node<T>(kp, k - 3 * ns, eth, tsqrt(Rd));
+    if (k >= 3 * ns) return ray_node<T>(kp, k - 3 * ns, eth, eD, tsqrt(Rd));
     T t, w;
     if (k < ns) {
         load2<T>(kp, 1, k, t, w);
@@ -357,30 +370,33 @@ struct Setup {
     C<T> ia[NT], v[NT], w[NT];
 };
 
-// One pair of angular nodes for NT terms; q = |1 - w t|^2.
-template <typename T>
-__device__ __forceinline__ T pair_q(T t, T wr, T wi, T w2, T m2wr);
-
-template <>
-__device__ __forceinline__ float pair_q<float>(float t, float wr, float wi, float w2, float m2wr)
+// |1 - w t|^2 for one angular node. Direct form (1 - wr t)^2 + (wi t)^2: its
+// rounding error relative to the result is ~ eps/|1 - w t| next to a pinch.
+// Horner form 1 + t (|w|^2 t - 2 wr): two FMAs, error ~ eps/|1 - w t|^2, used
+// only for compressed rules, whose selection keeps |1 - w t| away from zero.
+__device__ __forceinline__ double q_direct(double t, double wr, double wi)
 {
-    // Horner form 1 + t (-2 wr + |w|^2 t): two FMAs
-    (void)wr;
-    (void)wi;
-    // clamp: rounding may take |1 - w t|^2 to zero or below next to a pinch
-    return fmaxf(fmaf(fmaf(w2, t, m2wr), t, 1.0f), 1e-30f);
-}
-
-template <>
-__device__ __forceinline__ double pair_q<double>(double t, double wr, double wi, double w2,
-                                                 double m2wr)
-{
-    // direct form (1 - wr t)^2 + (wi t)^2: no cancellation near a pinch
-    (void)w2;
-    (void)m2wr;
     double dr = fma(-wr, t, 1.0);
     double di = wi * t;
     return fma(dr, dr, di * di);
+}
+__device__ __forceinline__ float q_direct(float t, float wr, float wi)
+{
+    float dr = fmaf(-wr, t, 1.0f);
+    float di = wi * t;
+    // keep the reciprocal finite if rounding lands on zero at a pinch
+    return fmaxf(fmaf(dr, dr, di * di), 1e-30f);
+}
+__device__ __forceinline__ df q_direct(df t, df wr, df wi)
+{
+    df dr = fma(-wr, t, df(1));
+    df di = wi * t;
+    return fma(dr, dr, di * di);
+}
+template <typename T>
+__device__ __forceinline__ T q_horner(T t, T w2, T m2wr)
+{
+    return fma(fma(w2, t, m2wr), t, T(1));
 }
 
 // Bernstein-ellipse parameter of the pole t = 1/w of 1/(1 - w t) for the
@@ -402,6 +418,8 @@ template <>
 __device__ __forceinline__ float rho_min<float>(const KParams &kp, int r) { return kp.rho_min32[r]; }
 template <>
 __device__ __forceinline__ float rho_min<double>(const KParams &kp, int r) { return kp.rho_min64[r]; }
+template <>
+__device__ __forceinline__ float rho_min<df>(const KParams &kp, int r) { return kp.rho_min64[r]; }
 
 // one node (tau, gamma, gamma tau) of a compressed rule in shared memory
 __device__ __forceinline__ void rule_node(const void *srules, int k, double &t, double &e,
@@ -412,6 +430,13 @@ __device__ __forceinline__ void rule_node(const void *srules, int k, double &t, 
     e = p[1];
     g = p[2];
 }
+__device__ __forceinline__ void rule_node(const void *srules, int k, df &t, df &e, df &g)
+{
+    const float2 *p = reinterpret_cast<const float2 *>(srules) + 3 * k;
+    t = df(p[0].x, p[0].y);
+    e = df(p[1].x, p[1].y);
+    g = df(p[2].x, p[2].y);
+}
 __device__ __forceinline__ void rule_node(const void *srules, int k, float &t, float &e, float &g)
 {
     float4 v = reinterpret_cast<const float4 *>(srules)[k];
@@ -420,11 +445,14 @@ __device__ __forceinline__ void rule_node(const void *srules, int k, float &t, f
     g = v.z;
 }
 
+// Angular sums A = sum e_j/q_j, B = sum g_j/q_j for NT terms; qmin (binary32
+// only) is the smallest q met, a measure of how close the node is to a pinch.
 template <typename T, int NP, int NT>
 __device__ __forceinline__ void pair_sums(const KParams &kp, const AngTab<T, tab_size<NP>()> &tab,
                                           int npair, const T *stab, const void *srules,
-                                          const C<T> (&w)[NT], T (&A)[NT], T (&B)[NT])
+                                          const C<T> (&w)[NT], T (&A)[NT], T (&B)[NT], T &qmin)
 {
+    constexpr bool f32 = sizeof(T) == 4;
     T w2[NT], m2wr[NT], A1[NT], B1[NT];
 #pragma unroll
     for (int s = 0; s < NT; ++s) {
@@ -432,6 +460,7 @@ __device__ __forceinline__ void pair_sums(const KParams &kp, const AngTab<T, tab
         m2wr[s] = T(-2) * w[s].r;
         A[s] = B[s] = A1[s] = B1[s] = T(0);
     }
+    T qm = T(1e30);
     // the smallest compressed rule that is exact to rounding level for every
     // term, made uniform over the lanes that run together
     int rule = kp.nrule;
@@ -454,7 +483,8 @@ __device__ __forceinline__ void pair_sums(const KParams &kp, const AngTab<T, tab
             rule_node(srules, off + k, t, e, g);
 #pragma unroll
             for (int s = 0; s < NT; ++s) {
-                T q = pair_q<T>(t, w[s].r, w[s].i, w2[s], m2wr[s]);
+                T q = f32 ? q_direct(t, w[s].r, w[s].i) : q_horner(t, w2[s], m2wr[s]);
+                if (f32) qm = fmin(qm, q);
                 T r = rcp(q);
                 A[s] = fma(e, r, A[s]);
                 B[s] = fma(g, r, B[s]);
@@ -466,7 +496,8 @@ __device__ __forceinline__ void pair_sums(const KParams &kp, const AngTab<T, tab
             const T t = tab.t[j], e = tab.e[j], g = tab.g[j];
 #pragma unroll
             for (int s = 0; s < NT; ++s) {
-                T q = pair_q<T>(t, w[s].r, w[s].i, w2[s], m2wr[s]);
+                T q = q_direct(t, w[s].r, w[s].i);
+                if (f32) qm = fmin(qm, q);
                 T r = rcp(q);
                 if (j & 1) {
                     A1[s] = fma(e, r, A1[s]);
@@ -483,7 +514,8 @@ __device__ __forceinline__ void pair_sums(const KParams &kp, const AngTab<T, tab
             const T t = stab[3 * j], e = stab[3 * j + 1], g = stab[3 * j + 2];
 #pragma unroll
             for (int s = 0; s < NT; ++s) {
-                T q = pair_q<T>(t, w[s].r, w[s].i, w2[s], m2wr[s]);
+                T q = q_direct(t, w[s].r, w[s].i);
+                if (f32) qm = fmin(qm, q);
                 T r = rcp(q);
                 A[s] = fma(e, r, A[s]);
                 B[s] = fma(g, r, B[s]);
@@ -495,58 +527,91 @@ __device__ __forceinline__ void pair_sums(const KParams &kp, const AngTab<T, tab
         A[s] += A1[s];
         B[s] += B1[s];
     }
+    qmin = qm;
+}
+
+// Per-pass constants of one point, computed once and reused for every node.
+template <typename T, int NT>
+struct PassPre {
+    int nt;
+    C<T> m2q[NT], m2k[NT];
+    C<T> cx2[NT];     // c_t 2x
+    C<T> omx[NT];     // Omega (x + M2_t)
+    int full[NT];     // k-leg is the whole dressed propagator
+    int same[NT];     // k-leg and (p-k)-leg share the pole: one reciprocal
+};
+
+template <typename T, int NT>
+__device__ __forceinline__ PassPre<T, NT> pass_pre(const KParams &kp, const Plan<T> &P, int pass,
+                                                   C<T> x)
+{
+    PassPre<T, NT> pp;
+    pp.nt = P.nterm[pass];
+    const T Om = T(kp.Omega);
+#pragma unroll
+    for (int s = 0; s < NT; ++s) {
+        const Term<T> &tm = P.term[pass][s < pp.nt ? s : 0];
+        pp.m2q[s] = tm.m2q;
+        pp.m2k[s] = tm.m2k;
+        pp.cx2[s] = tm.c * (T(2) * x);
+        pp.omx[s] = Om * (x + tm.m2q);
+        pp.full[s] = tm.full;
+        pp.same[s] = !tm.full && tm.m2k.r == tm.m2q.r && tm.m2k.i == tm.m2q.i;
+    }
+    return pp;
 }
 
 // Contribution of one node of one pass: Jt * sum_t c_t P1_t(y)/(y + M2_t) *
 // 2x/a_t * S_t, with the (1 + |y|)^2 scale moved from Jt onto the fractions.
+// `mag` receives the node's error scale (binary32 and cond output only) and
+// `qmin` the smallest |1 - w t|^2 of its angular sums (binary32).
 template <typename T, int NP, int NT>
 __device__ __forceinline__ C<T> node_value(const KParams &kp, const AngTab<T, tab_size<NP>()> &tab,
-                                           const T *stab, const void *srules, const Plan<T> &P,
-                                           int pass, C<T> x, const Node<T> &nd, T &mag)
+                                           const T *stab, const void *srules,
+                                           const PassPre<T, NT> &pp, C<T> x, const Node<T> &nd,
+                                           T &mag, T &qmin)
 {
-    const int nt = P.nterm[pass];
     C<T> ia[NT], v[NT], w[NT];
 #pragma unroll
     for (int s = 0; s < NT; ++s) {
-        const Term<T> &tm = P.term[pass][s < nt ? s : 0];
-        C<T> a = x + nd.y + tm.m2q;
+        C<T> a = x + nd.y + pp.m2q[s];
         ia[s] = cinv(a);
         v[s] = T(4) * (nd.y * ia[s]);
         w[s] = (x * v[s]) * ia[s];
     }
     T A[NT], B[NT];
-    pair_sums<T, NP, NT>(kp, tab, kp.npair, stab, srules, w, A, B);
-    const T Om = T(kp.Omega), Om1 = T(kp.Omega1), del = T(kp.delta);
+    pair_sums<T, NP, NT>(kp, tab, kp.npair, stab, srules, w, A, B, qmin);
+    const T Om1 = T(kp.Omega1), del = T(kp.delta);
     const bool want_mag = sizeof(T) == 4 || kp.cond_out != nullptr;
-    C<T> x2 = T(2) * x;
     C<T> sum = {T(0), T(0)};
     mag = T(0);
 #pragma unroll
     for (int s = 0; s < NT; ++s) {
-        if (s >= nt) break;
-        const Term<T> &tm = P.term[pass][s];
+        if (s >= pp.nt) break;
         C<T> T2 = {A[s] - w[s].r * B[s], w[s].i * B[s]};
-        C<T> lead = (del * nd.y - Om * (x + tm.m2q)) * ia[s] - Om1 * w[s];
+        C<T> lead = (del * nd.y - pp.omx[s]) * ia[s] - Om1 * w[s];
         C<T> vw = (v[s] - w[s]) * w[s];
         C<T> S = lead + vw * T2;
-        // size of S without cancellation between its parts (A, B > 0), in
-        // the |re| + |im| norm (no square roots); only the error estimate of
-        // the binary32 path and the optional cond output use it
-        T Sabs = want_mag ? cabs1(lead) + cabs1(vw) * (A[s] + cabs1(w[s]) * B[s]) : T(0);
-        // (1 + |y|) P1(y)
+        // (1 + |y|)^2 P1(y) / (y + M2)
+        C<T> pq = nd.sc * cinv(nd.y + pp.m2q[s]);
         C<T> p1;
-        if (tm.full) {
+        if (pp.same[s]) {
+            p1 = pq;
+        } else if (pp.full[s]) {
             C<T> yp = cvt<T>(kp.pc.yp_re, kp.pc.yp_im);
             C<T> Rp = cvt<T>(kp.pc.Rp_re, kp.pc.Rp_im);
-            p1 = Rp * cinv(nd.y - yp) + conj(Rp) * cinv(nd.y - conj(yp));
-            p1 = nd.sc * p1;
+            p1 = nd.sc * (Rp * cinv(nd.y - yp) + conj(Rp) * cinv(nd.y - conj(yp)));
         } else {
-            p1 = nd.sc * cinv(nd.y + tm.m2k);
+            p1 = nd.sc * cinv(nd.y + pp.m2k[s]);
         }
-        C<T> pq = nd.sc * cinv(nd.y + tm.m2q);
-        C<T> f = (tm.c * (p1 * pq)) * (x2 * ia[s]);
+        C<T> f = (pp.cx2[s] * (p1 * pq)) * ia[s];
         sum = sum + f * S;
-        if (want_mag) mag += cabs1(f) * Sabs;
+        if (want_mag) {
+            // rounding scale of S: its parts without cancellation; A and B are
+            // positive sums that carry the sensitivity to w and to each q
+            T Sabs = cabs1(lead) + cabs1(vw) * (A[s] + cabs1(w[s]) * B[s]);
+            mag += cabs1(f) * Sabs;
+        }
     }
     if (want_mag) mag *= cabs1(nd.Jt);
     return nd.Jt * sum;
@@ -572,11 +637,22 @@ __device__ __forceinline__ void two_sum_add(T &s, T &c, T v)
     c += err;
 }
 
-template <typename T>
-__device__ __forceinline__ void acc_add(Acc<T> &a, C<T> v)
+// binary32: compensated (TwoSum) radial sums; binary64: plain sums (at most
+// n_r/32 terms per lane, error far below the FP64 tolerance)
+__device__ __forceinline__ void acc_add(Acc<float> &a, C<float> v)
 {
     two_sum_add(a.sr, a.cr, v.r);
     two_sum_add(a.si, a.ci, v.i);
+}
+__device__ __forceinline__ void acc_add(Acc<double> &a, C<double> v)
+{
+    a.sr += v.r;
+    a.si += v.i;
+}
+__device__ __forceinline__ void acc_add(Acc<df> &a, C<df> v)
+{
+    a.sr = a.sr + v.r;
+    a.si = a.si + v.i;
 }
 
 __device__ __forceinline__ double warp_sum(double v)
@@ -602,33 +678,49 @@ __device__ __forceinline__ void point_x(const KParams &kp, int64_t p, double &xr
     }
 }
 
-// Sum over one point's contour, per lane, into acc.
+// One pass of a point's contour, the lane's share of its nodes.
+template <typename T, int NP, int NTT>
+__device__ __forceinline__ void run_pass(const KParams &kp, const AngTab<T, tab_size<NP>()> &tab,
+                                         const T *stab, const void *srules, const Plan<T> &P,
+                                         int pass, C<T> x, C<T> eD, int lane, Acc<T> &acc,
+                                         T &amag, T &qall)
+{
+    const PassPre<T, NTT> pp = pass_pre<T, NTT>(kp, P, pass, x);
+    const bool ray = P.kind[pass] == PASS_RAY;
+    const int nn = ray ? kp.n_r : 3 * kp.n_s + kp.n_r;
+    for (int k = lane; k < nn; k += 32) {
+        Node<T> nd = ray ? ray_node<T>(kp, k, P.eth, eD, T(0))
+                         : detour_node<T>(kp, k, P.eth, eD, P.yp, x);
+        T mag, qm;
+        C<T> v = node_value<T, NP, NTT>(kp, tab, stab, srules, pp, x, nd, mag, qm);
+        acc_add(acc, v);
+        amag += mag;
+        qall = fmin(qall, qm);
+    }
+}
+
+// Sum over one point's contour, per lane, into acc; returns the point's
+// number of contour nodes.
 template <typename T, int NP, int NT>
 __device__ __forceinline__ int point_sum(const KParams &kp, const AngTab<T, tab_size<NP>()> &tab,
-                                          const T *stab, const void *srules, double xr, double xi,
-                                          int lane,
-                                          int lane_stride, int lane_count_nodes_limit,
-                                          Acc<T> &acc, T &amag)
+                                         const T *stab, const void *srules, double xr, double xi,
+                                         int lane, Acc<T> &acc, T &amag, T &qall)
 {
-    Plan<T> P = make_plan<T>(kp, xr, xi);
-    C<T> x = cvt<T>(xr, xi);
-    (void)lane_count_nodes_limit;
+    const Plan<T> P = make_plan<T>(kp, xr, xi);
+    const C<T> x = cvt<T>(xr, xi);
+    // e^{i D theta} of the ray, once per point
+    const C<T> e2 = P.eth * P.eth;
+    const C<T> eD = kp.dim == 4 ? e2 * e2 : e2 * P.eth;
     int total = 0;
-    for (int pass = 0; pass < P.npass; ++pass) {
-        const int nn = P.kind[pass] == PASS_RAY ? kp.n_r : 3 * kp.n_s + kp.n_r;
-        total += nn;
-        for (int k = lane; k < nn; k += lane_stride) {
-            Node<T> nd = P.kind[pass] == PASS_RAY ? ray_node<T>(kp, k, P.eth, T(0))
-                                                  : detour_node<T>(kp, k, P.eth, P.yp, x);
-            C<T> v;
-            T mag;
-            if (P.nterm[pass] == 2)
-                v = node_value<T, NP, (NT > 1 ? 2 : 1)>(kp, tab, stab, srules, P, pass, x, nd, mag);
-            else
-                v = node_value<T, NP, 1>(kp, tab, stab, srules, P, pass, x, nd, mag);
-            acc_add(acc, v);
-            amag += mag;
-        }
+#pragma unroll
+    for (int pass = 0; pass < 2; ++pass) {
+        if (pass >= P.npass) break;
+        total += P.kind[pass] == PASS_RAY ? kp.n_r : 3 * kp.n_s + kp.n_r;
+        if (NT > 1 && P.nterm[pass] == 2)
+            run_pass<T, NP, (NT > 1 ? 2 : 1)>(kp, tab, stab, srules, P, pass, x, eD, lane, acc,
+                                             amag, qall);
+        else
+            run_pass<T, NP, 1>(kp, tab, stab, srules, P, pass, x, eD, lane, acc, amag, qall);
     }
     return total;
 }
@@ -666,23 +758,30 @@ __device__ __forceinline__ void eval_point(const KParams &kp, const AngTab<T, ta
     }
     Acc<T> acc;
     acc.init();
-    T amag = T(0);
-    int nodes = point_sum<T, NP, NT>(kp, tab, stab, srules, xr, xi, lane, 32, 0, acc, amag);
+    T amag = T(0), qall = T(1e30);
+    int nodes = point_sum<T, NP, NT>(kp, tab, stab, srules, xr, xi, lane, acc, amag, qall);
     if (kp.node_count && lane == 0)
         atomicAdd(kp.node_count, (unsigned long long)nodes * (unsigned long long)(2 * kp.npair));
     double sr = warp_sum((double)acc.sr + (double)acc.cr);
     double si = warp_sum((double)acc.si + (double)acc.ci);
     double cond = kp.K_D * warp_sum((double)amag);
+    float qpt = (float)qall;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) qpt = fminf(qpt, __shfl_xor_sync(0xffffffffu, qpt, o));
     if (lane == 0) {
         double gr = kp.K_D * sr - kp.g0mu[0], gi = kp.K_D * si - kp.g0mu[1];
         out[0] = gr;
         out[1] = gi;
         if (kp.cond_out) kp.cond_out[p] = cond;
         if (mode == MODE_BULK32 && kp.mixed_rtol > 0.0) {
-            // rounding error of the binary32 sum: a few units of 2^-24 on
-            // every node's magnitude; hand the point over if that is too much
-            double est = 8.0 * 5.9604644775390625e-8 * cond;
-            if (!(est <= kp.mixed_rtol * sqrt(gr * gr + gi * gi))) list_append(kp, p);
+            // rounding error of the binary32 sum: a small multiple of 2^-24
+            // times the nodes' error scales. Next to a pinch (some node with
+            // |1 - w t| < 0.03) the discrete sum is so sensitive to the
+            // binary32 rounding of x and of the nodes that no such bound
+            // holds; those points go to binary64 too.
+            double est = kMixedErrFactor * 5.9604644775390625e-8 * cond;
+            if (!(est <= kp.mixed_rtol * sqrt(gr * gr + gi * gi)) || qpt < kMixedPinchQ)
+                list_append(kp, p);
         }
     }
 }
@@ -693,9 +792,11 @@ template <>
 __device__ __forceinline__ const void *rules_of<double>(const KParams &kp) { return kp.rules64; }
 template <>
 __device__ __forceinline__ const void *rules_of<float>(const KParams &kp) { return kp.rules32; }
+template <>
+__device__ __forceinline__ const void *rules_of<df>(const KParams &kp) { return kp.rules_df; }
 
 template <typename T>
-__host__ __device__ constexpr int rule_bytes() { return sizeof(T) == 8 ? 24 : 16; }
+__host__ __device__ constexpr int rule_bytes() { return sizeof(T) == 8 ? 24 : 16; }   // double, df: 3 x 8
 
 // bytes of shared memory: the full pair table (generic kernels only), 16-byte
 // aligned, then the compressed rules
@@ -803,15 +904,19 @@ g0mu_kernel(const __grid_constant__ KParams kp,
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
     Plan<double> P = make_plan<double>(kp, mu2, 0.0);
     C<double> x = {mu2, 0.0};
+    C<double> e2 = P.eth * P.eth;
+    C<double> eD = kp.dim == 4 ? e2 * e2 : e2 * P.eth;
     double sr = 0.0, si = 0.0;
     // the real-axis point has one ray pass
     const int nn = kp.n_r;
+    const PassPre<double, 2> pp2 = pass_pre<double, 2>(kp, P, 0, x);
+    const PassPre<double, 1> pp1 = pass_pre<double, 1>(kp, P, 0, x);
     for (int k = warp * 32 + lane; k < nn; k += nwarps * 32) {
-        Node<double> nd = ray_node<double>(kp, k, P.eth, 0.0);
-        double mag;
+        Node<double> nd = ray_node<double>(kp, k, P.eth, eD, 0.0);
+        double mag, qm;
         C<double> v = P.nterm[0] == 2
-                          ? node_value<double, NP, 2>(kp, tab, stab, srules, P, 0, x, nd, mag)
-                          : node_value<double, NP, 1>(kp, tab, stab, srules, P, 0, x, nd, mag);
+                          ? node_value<double, NP, 2>(kp, tab, stab, srules, pp2, x, nd, mag, qm)
+                          : node_value<double, NP, 1>(kp, tab, stab, srules, pp1, x, nd, mag, qm);
         sr += v.r;
         si += v.i;
     }
@@ -885,6 +990,8 @@ template <>
 const double *gtab_of<double>(const DevTables &tb) { return tb.ang64; }
 template <>
 const float *gtab_of<float>(const DevTables &tb) { return tb.ang32; }
+template <>
+const df *gtab_of<df>(const DevTables &tb) { return reinterpret_cast<const df *>(tb.ang_df); }
 
 template <typename T, int NP, int NT>
 static cudaError_t run_eval(const KParams &kp, const DevTables &tb, cudaStream_t st)
@@ -948,17 +1055,23 @@ static cudaError_t run_batch_np(const BatchLaunch &bl, const DevTables &tb, cuda
     }
 }
 
-cudaError_t launch_batch(const BatchLaunch &bl, const DevTables &tb, bool fp32, bool two_terms,
+cudaError_t launch_batch(const BatchLaunch &bl, const DevTables &tb, int arith, bool two_terms,
                          cudaStream_t st)
 {
-    if (fp32) return two_terms ? run_batch_np<float, 2>(bl, tb, st) : run_batch_np<float, 1>(bl, tb, st);
+    if (arith == ARITH_F32)
+        return two_terms ? run_batch_np<float, 2>(bl, tb, st) : run_batch_np<float, 1>(bl, tb, st);
+    if (arith == ARITH_DF)
+        return two_terms ? run_batch_np<df, 2>(bl, tb, st) : run_batch_np<df, 1>(bl, tb, st);
     return two_terms ? run_batch_np<double, 2>(bl, tb, st) : run_batch_np<double, 1>(bl, tb, st);
 }
 
-cudaError_t launch_eval(const KParams &kp, const DevTables &tb, bool fp32, cudaStream_t st)
+cudaError_t launch_eval(const KParams &kp, const DevTables &tb, int arith, cudaStream_t st)
 {
     const bool two = kp.pc.kind == 2;
-    if (fp32) return two ? run_eval_np<float, 2>(kp, tb, st) : run_eval_np<float, 1>(kp, tb, st);
+    if (arith == ARITH_F32)
+        return two ? run_eval_np<float, 2>(kp, tb, st) : run_eval_np<float, 1>(kp, tb, st);
+    if (arith == ARITH_DF)
+        return two ? run_eval_np<df, 2>(kp, tb, st) : run_eval_np<df, 1>(kp, tb, st);
     return two ? run_eval_np<double, 2>(kp, tb, st) : run_eval_np<double, 1>(kp, tb, st);
 }
 

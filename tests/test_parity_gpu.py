@@ -181,3 +181,19 @@ def test_production_grid_sampled(precision, m2):
     x = oracle.grid_points(*rect, 1024, 1024)[idx]
     ref = oracle.eval_points(prop, oracle_params(par), x)
     assert_parity(G[idx], ref, RTOL[precision], x, f"production m2={m2} {precision}")
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("dim", [3, 4])
+def test_dressed_full_size_sampled(precision, dim):
+    """The dressed workload at full size: 512 x 512 over [-8,4] x [-4,4],
+    1024 x 128 nodes, two seeded (a, b, c) draws, 48 sampled points each."""
+    rect = si.grid_rect("small")
+    par = dict(dim=dim, mu2=1.0, n_radial=1024, n_angular=128, precision=precision)
+    for k, (a, b, c) in enumerate(si.dressed_draws(3, 2)):
+        prop = {"kind": "dressed", "a": a, "b": b, "c": c}
+        G = run_grid(prop, par, rect, 512, 512).ravel()
+        idx = si.sample_indices(300 + k, 512 * 512, 48)
+        x = oracle.grid_points(*rect, 512, 512)[idx]
+        ref = oracle.eval_points(prop, oracle_params(par), x)
+        assert_parity(G[idx], ref, RTOL[precision], x, f"dressed 512^2 D={dim} draw {k} {precision}")
