@@ -41,7 +41,7 @@ extern "C" {
 #endif
 
 #define GFC_VERSION_MAJOR 1
-#define GFC_VERSION_MINOR 0
+#define GFC_VERSION_MINOR 1
 
 enum {
     GFC_OK = 0,
@@ -75,9 +75,12 @@ typedef struct {
 
 typedef enum {
     GFC_FP64 = 0,    /* every step in IEEE binary64                            */
-    GFC_MIXED = 1    /* angular sums and per-node set-up in binary32 with
+    GFC_MIXED = 1,   /* angular sums and per-node set-up in binary32 with
                         compensated binary32 radial sums; binary64 for the
                         epilogue and for every point in the binary64 band     */
+    GFC_F32X2 = 2    /* every step in double-float arithmetic (a value is the
+                        sum of two binary32 numbers, ~48 bits) on the binary32
+                        pipes; same tolerance target as GFC_FP64               */
 } gfc_precision;
 
 typedef struct {
@@ -100,6 +103,8 @@ typedef struct {
                               estimated rounding error above mixed_rtol |G| is
                               evaluated again in binary64 (default 1e-6;
                               0 turns this off, leaving the cut band only)     */
+    int mixed_fallback;    /* MIXED: arithmetic of the points routed out of
+                              binary32: GFC_FP64 (default) or GFC_F32X2        */
 } gfc_params;
 
 /* Cell-centred grid of Kernel 1 (Sect. 4): x_ij = re0 + (i + 1/2)(re1-re0)/m
@@ -119,6 +124,9 @@ typedef struct {
                                   angular nodes (all passes; binary32 and
                                   binary64 evaluations both counted)            */
     int kernel_launches;       /* kernels enqueued by the call                  */
+    int64_t pairs_evaluated;   /* angular +-psi pairs the kernels evaluated; the
+                                  compressed angular rules make this smaller
+                                  than node_evals / 2 at the same result        */
 } gfc_eval_stats;
 
 const char *gfc_strerror(int status);
@@ -127,7 +135,7 @@ const char *gfc_last_error(void);
 int gfc_version(int *major, int *minor);
 
 /* Defaults: D = 4, mu2 = 1, 2048 x 256 nodes, L = 1, r = 0.1, FP64,
- * cut_band 0.05, pinch_angle 0, mixed_rtol 1e-6. */
+ * cut_band 0.05, pinch_angle 0, mixed_rtol 1e-6, mixed_fallback FP64. */
 int gfc_params_default(gfc_params *p);
 
 /* Steps 4-5 on caller-given points: x and G are DEVICE arrays of npts

@@ -15,7 +15,8 @@ from . import build as _build
 GFC_OK, GFC_EINVAL, GFC_ENOMEM, GFC_EBUDGET, GFC_ECUDA = 0, -1, -2, -3, -4
 GFC_ETIMEOUT, GFC_ECANCELED, GFC_EBUSY, GFC_ENOTFOUND = -5, -6, -7, -8
 GFC_PROP_SCALAR, GFC_PROP_CPAIR, GFC_PROP_DRESSED = 0, 1, 2
-GFC_FP64, GFC_MIXED = 0, 1
+GFC_FP64, GFC_MIXED, GFC_F32X2 = 0, 1, 2
+_PRECISION = {"fp64": GFC_FP64, "mixed": GFC_MIXED, "f32x2": GFC_F32X2}
 
 
 class GfcError(RuntimeError):
@@ -36,7 +37,8 @@ class _Params(ctypes.Structure):
                 ("n_radial", ctypes.c_int), ("n_angular", ctypes.c_int),
                 ("radial_scale", ctypes.c_double), ("detour_radius", ctypes.c_double),
                 ("precision", ctypes.c_int), ("cut_band", ctypes.c_double),
-                ("pinch_angle", ctypes.c_double), ("mixed_rtol", ctypes.c_double)]
+                ("pinch_angle", ctypes.c_double), ("mixed_rtol", ctypes.c_double),
+                ("mixed_fallback", ctypes.c_int)]
 
 
 class _Grid(ctypes.Structure):
@@ -47,7 +49,8 @@ class _Grid(ctypes.Structure):
 
 class _EvalStats(ctypes.Structure):
     _fields_ = [("points", ctypes.c_int64), ("points_fp64", ctypes.c_int64),
-                ("node_evals", ctypes.c_int64), ("kernel_launches", ctypes.c_int)]
+                ("node_evals", ctypes.c_int64), ("kernel_launches", ctypes.c_int),
+                ("pairs_evaluated", ctypes.c_int64)]
 
 
 class _ServerStats(ctypes.Structure):
@@ -149,7 +152,7 @@ def make_prop(spec) -> _Prop:
 
 def make_params(spec=None, **kw) -> _Params:
     """Defaults of gfc_params_default, overridden by ``spec``/keywords;
-    ``precision`` may be 'fp64' or 'mixed'."""
+    ``precision`` and ``mixed_fallback`` may be 'fp64', 'mixed' or 'f32x2'."""
     if isinstance(spec, _Params) and not kw:
         return spec
     lib = load_library()
@@ -158,8 +161,8 @@ def make_params(spec=None, **kw) -> _Params:
     d = dict(spec or {})
     d.update(kw)
     for k, v in d.items():
-        if k == "precision":
-            v = {"fp64": GFC_FP64, "mixed": GFC_MIXED}.get(v, v)
+        if k in ("precision", "mixed_fallback"):
+            v = _PRECISION.get(v, v)
         if not hasattr(q, k):
             raise ValueError(f"unknown parameter {k!r}")
         setattr(q, k, type(getattr(q, k))(v))
@@ -262,13 +265,14 @@ class EvalStats:
     points_fp64: int
     node_evals: int
     kernel_launches: int
+    pairs_evaluated: int
 
 
 def last_stats() -> EvalStats:
     lib = load_library()
     s = _EvalStats()
     _check(lib.gfc_last_stats(ctypes.byref(s)), "gfc_last_stats")
-    return EvalStats(s.points, s.points_fp64, s.node_evals, s.kernel_launches)
+    return EvalStats(s.points, s.points_fp64, s.node_evals, s.kernel_launches, s.pairs_evaluated)
 
 
 def version():

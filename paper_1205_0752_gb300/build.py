@@ -14,6 +14,10 @@ LIB = os.path.join(BUILD, "libgfc.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["gfc_kernels.cu", "gfc_capi.cpp", "gfc_server.cpp", "gfc_noalloc.cu"]
+# gfc_eval_inst.cu is compiled once per (arithmetic, unrolled angular pair
+# count) so that the kernel instantiations build in parallel; double-float
+# has the generic loop only
+INSTANCES = [(t, n) for t in ("double", "float") for n in (32, 64, 128, 0)] + [("df", 0)]
 
 
 def _nvcc() -> str:
@@ -40,11 +44,14 @@ def build(force: bool = False, verbose: bool = False) -> str:
     # kernels' explicitly rounded grid arithmetic on every host architecture
     common = ARCH + ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-O2,-ffp-contract=off",
                      "-I", INCLUDE, "-I", CSRC]
-    srcs = [s for s in SOURCES if os.path.exists(os.path.join(CSRC, s))]
+    units = [(s, []) for s in SOURCES if os.path.exists(os.path.join(CSRC, s))]
+    units += [("gfc_eval_inst.cu", [f"-DGFC_INST_T={t}", f"-DGFC_INST_NP={n}"]) for t, n in INSTANCES]
 
-    def compile_one(src):
-        obj = os.path.join(BUILD, src + f".{os.getpid()}.o")
-        cmd = [nvcc] + common + ["-c", os.path.join(CSRC, src), "-o", obj]
+    def compile_one(unit):
+        src, defs = unit
+        tag = "".join(d.split("=")[1] for d in defs)
+        obj = os.path.join(BUILD, src + tag + f".{os.getpid()}.o")
+        cmd = [nvcc] + common + defs + ["-c", os.path.join(CSRC, src), "-o", obj]
         if src.endswith(".cu"):
             cmd += ["-Xptxas", "-v"] if verbose else []
         r = subprocess.run(cmd, capture_output=True, text=True)
@@ -54,8 +61,11 @@ def build(force: bool = False, verbose: bool = False) -> str:
             sys.stderr.write(r.stderr)
         return obj
 
-    with ThreadPoolExecutor(max_workers=len(srcs)) as ex:
-        objs = list(ex.map(compile_one, srcs))
+    # largest units first, so the longest compiles start at once
+    units.sort(key=lambda u: (not u[1], u[0] != "gfc_kernels.cu"))
+    workers = max(1, min(len(units), os.cpu_count() or 1))
+    with ThreadPoolExecutor(max_workers=workers) as ex:
+        objs = list(ex.map(compile_one, units))
     tmp = LIB + f".{os.getpid()}.tmp"
     cmd = [nvcc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lpthread"]
     r = subprocess.run(cmd, capture_output=True, text=True)

@@ -14,6 +14,7 @@
 #include <vector>
 
 #include "gfc.h"
+#include "gfc_df.h"
 #include "gfc_internal.h"
 
 namespace gfc {
@@ -99,8 +100,11 @@ struct Tables {
     double L;
     double2 *rad64 = nullptr, *seg64 = nullptr, *arc64 = nullptr;
     float2 *rad32 = nullptr, *seg32 = nullptr, *arc32 = nullptr;
+    float4 *rad_df = nullptr, *seg_df = nullptr, *arc_df = nullptr;
     double *ang64 = nullptr;
     float *ang32 = nullptr;
+    float2 *ang_df = nullptr;
+    float2 *rules_df = nullptr;
     std::vector<double> t, e, g;
     double Omega = 0, Omega1 = 0, delta = 0;
     // compressed angular rules
@@ -263,13 +267,13 @@ static void build_rules(Tables &T, std::vector<double> &r64, std::vector<float4>
 // Per (device, stream) scratch: calls on one stream are ordered by the
 // stream, so they can share it; calls on different streams get their own.
 // counters: [0] work counter of the first launch, [1] of the second, [2]
-// length of the binary64 list, [3] node-evaluation count; the G0(mu2) kernel
-// of every call zeroes them.
+// length of the binary64 list, [3] node-evaluation count, [4] angular pairs
+// evaluated; the G0(mu2) kernel of every call zeroes them.
 struct Scratch {
     double *partials = nullptr;   // 2 * kMaxG0Warps
     unsigned *ticket = nullptr;
     double *g0mu = nullptr;       // 2
-    unsigned long long *counters = nullptr;   // 4
+    unsigned long long *counters = nullptr;   // kCounters
     int64_t *list = nullptr;      // binary64 list of the mixed precision
     int64_t list_cap = 0;
     double *stage_x = nullptr, *stage_G = nullptr;   // host-path staging
@@ -306,6 +310,11 @@ static int free_tables(Tables &T)
     cudaFree(T.ang32);
     cudaFree(T.rules64);
     cudaFree(T.rules32);
+    cudaFree(T.rad_df);
+    cudaFree(T.seg_df);
+    cudaFree(T.arc_df);
+    cudaFree(T.ang_df);
+    cudaFree(T.rules_df);
     return GFC_OK;
 }
 
@@ -388,12 +397,30 @@ static int build_tables(Tables &T)
     std::vector<double> r64;
     std::vector<float4> r32;
     build_rules(T, r64, r32);
+    // double-float copies (hi = nearest binary32, lo = the rest)
+    auto dfv = [](double a) { df v(a); return make_float2(v.hi, v.lo); };
+    auto df4 = [](double a, double b) {
+        df u(a), v(b);
+        return make_float4(u.hi, u.lo, v.hi, v.lo);
+    };
+    std::vector<float4> radD(T.n_r), segD(ns), arcD(ns);
+    for (int k = 0; k < T.n_r; ++k) radD[k] = df4(rad64[k].x, rad64[k].y);
+    for (int k = 0; k < ns; ++k) {
+        segD[k] = df4(seg64[k].x, seg64[k].y);
+        arcD[k] = df4(arc64[k].x, arc64[k].y);
+    }
+    std::vector<float2> angD(3 * np), rulesD(r64.size());
+    for (int j = 0; j < 3 * np; ++j) angD[j] = dfv(ang64[j]);
+    for (size_t j = 0; j < r64.size(); ++j) rulesD[j] = dfv(r64[j]);
     int st;
     if ((st = upload(&T.rad64, rad64, T.bytes)) || (st = upload(&T.rad32, rad32, T.bytes)) ||
         (st = upload(&T.seg64, seg64, T.bytes)) || (st = upload(&T.seg32, seg32, T.bytes)) ||
         (st = upload(&T.arc64, arc64, T.bytes)) || (st = upload(&T.arc32, arc32, T.bytes)) ||
         (st = upload(&T.ang64, ang64, T.bytes)) || (st = upload(&T.ang32, ang32, T.bytes)) ||
-        (st = upload(&T.rules64, r64, T.bytes)) || (st = upload(&T.rules32, r32, T.bytes)))
+        (st = upload(&T.rules64, r64, T.bytes)) || (st = upload(&T.rules32, r32, T.bytes)) ||
+        (st = upload(&T.rad_df, radD, T.bytes)) || (st = upload(&T.seg_df, segD, T.bytes)) ||
+        (st = upload(&T.arc_df, arcD, T.bytes)) || (st = upload(&T.ang_df, angD, T.bytes)) ||
+        (st = upload(&T.rules_df, rulesD, T.bytes)))
         return st;
     return GFC_OK;
 }
@@ -444,7 +471,7 @@ int get_scratch(int dev, cudaStream_t s, Scratch **out)
     if ((e = cudaMalloc((void **)&S->partials, sizeof(double) * 2 * kMaxG0Warps)) != cudaSuccess ||
         (e = cudaMalloc((void **)&S->ticket, sizeof(unsigned))) != cudaSuccess ||
         (e = cudaMalloc((void **)&S->g0mu, sizeof(double) * 2)) != cudaSuccess ||
-        (e = cudaMalloc((void **)&S->counters, sizeof(unsigned long long) * 4)) != cudaSuccess) {
+        (e = cudaMalloc((void **)&S->counters, sizeof(unsigned long long) * kCounters)) != cudaSuccess) {
         cudaFree(S->partials);
         cudaFree(S->ticket);
         cudaFree(S->g0mu);
@@ -473,8 +500,10 @@ static int check_params(const gfc_params *p)
     if (!(p->radial_scale > 0.0) || !std::isfinite(p->radial_scale))
         return fail(GFC_EINVAL, "radial_scale must be > 0");
     if (!(p->detour_radius > 0.0)) return fail(GFC_EINVAL, "detour_radius must be > 0");
-    if (p->precision != GFC_FP64 && p->precision != GFC_MIXED)
-        return fail(GFC_EINVAL, "precision must be GFC_FP64 or GFC_MIXED");
+    if (p->precision != GFC_FP64 && p->precision != GFC_MIXED && p->precision != GFC_F32X2)
+        return fail(GFC_EINVAL, "precision must be GFC_FP64, GFC_MIXED or GFC_F32X2");
+    if (p->mixed_fallback != GFC_FP64 && p->mixed_fallback != GFC_F32X2)
+        return fail(GFC_EINVAL, "mixed_fallback must be GFC_FP64 or GFC_F32X2");
     if (!(p->cut_band >= 0.0) || !(p->pinch_angle >= 0.0) || !(p->mixed_rtol >= 0.0))
         return fail(GFC_EINVAL, "cut_band, pinch_angle and mixed_rtol must be >= 0");
     return GFC_OK;
@@ -547,6 +576,10 @@ static void fill_kparams_tables(KParams &kp, const gfc_params *p, const Tables &
     kp.seg32 = T.seg32;
     kp.arc64 = T.arc64;
     kp.arc32 = T.arc32;
+    kp.rad_df = T.rad_df;
+    kp.seg_df = T.seg_df;
+    kp.arc_df = T.arc_df;
+    kp.rules_df = T.rules_df;
     kp.L = p->radial_scale;
     kp.r_detour = p->detour_radius;
     // K_D = S_(D-2)/(2 pi)^D, eq. 11 for D = 4
@@ -580,6 +613,7 @@ static void fill_kparams(KParams &kp, const gfc_params *p, const Tables &T, cons
     kp.list = S.list;
     kp.list_count = S.counters + 2;
     kp.node_count = S.counters + 3;
+    kp.pair_count = S.counters + 4;
 }
 
 static int grow_list(Scratch &S, int64_t n)
@@ -599,6 +633,7 @@ static DevTables dev_tables(const Tables &T)
     DevTables tb;
     tb.ang64 = T.ang64;
     tb.ang32 = T.ang32;
+    tb.ang_df = T.ang_df;
     tb.t = T.t.data();
     tb.e = T.e.data();
     tb.g = T.g.data();
@@ -643,25 +678,25 @@ static int run(const gfc_propagator *prop, const gfc_params *p, KParams kp_point
     if (e != cudaSuccess) return cuda_fail(e, "g0mu launch");
     stats.kernel_launches = 1;
     if (kp.npts > 0) {
-        if (p->precision == GFC_FP64) {
+        if (p->precision != GFC_MIXED) {
             kp.mode = MODE_ALL;
             kp.counter = S->counters;
-            e = launch_eval(kp, tb, false, st);
+            e = launch_eval(kp, tb, p->precision == GFC_F32X2 ? ARITH_DF : ARITH_F64, st);
             if (e != cudaSuccess) return cuda_fail(e, "eval launch");
             stats.kernel_launches += 1;
         } else {
             kp.mode = MODE_BULK32;
             kp.counter = S->counters;
-            e = launch_eval(kp, tb, true, st);
+            e = launch_eval(kp, tb, ARITH_F32, st);
             if (e != cudaSuccess) return cuda_fail(e, "eval launch (binary32)");
             kp.mode = MODE_LIST64;
             kp.counter = S->counters + 1;
-            e = launch_eval(kp, tb, false, st);
+            e = launch_eval(kp, tb, p->mixed_fallback == GFC_F32X2 ? ARITH_DF : ARITH_F64, st);
             if (e != cudaSuccess) return cuda_fail(e, "eval launch (binary64 list)");
             stats.kernel_launches += 2;
         }
     }
-    stats.points_fp64 = p->precision == GFC_FP64 ? kp.npts : -1;
+    stats.points_fp64 = p->precision != GFC_MIXED ? kp.npts : -1;
     stats.node_evals = -1;
     g_last_stats = stats;
     g_last_call.counters = S->counters;
@@ -738,6 +773,7 @@ int gfc_params_default(gfc_params *p)
     p->cut_band = 0.05;
     p->pinch_angle = 0.0;
     p->mixed_rtol = 1e-6;
+    p->mixed_fallback = GFC_FP64;
     return GFC_OK;
 }
 
@@ -886,12 +922,13 @@ int gfc_last_stats(gfc_eval_stats *out)
     if (!out) return fail(GFC_EINVAL, "out is NULL");
     *out = g_last_stats;
     if (g_last_call.counters) {
-        unsigned long long c[4];
+        unsigned long long c[kCounters];
         cudaError_t e = cudaStreamSynchronize(g_last_call.stream);
         if (e == cudaSuccess)
             e = cudaMemcpy(c, g_last_call.counters, sizeof c, cudaMemcpyDeviceToHost);
         if (e != cudaSuccess) return cuda_fail(e, "reading the call's counters");
         out->node_evals = (int64_t)c[3];
+        out->pairs_evaluated = (int64_t)c[4];
         if (g_last_call.precision == GFC_MIXED) out->points_fp64 = (int64_t)c[2];
     }
     return GFC_OK;

@@ -32,6 +32,8 @@ struct df {
     __host__ __device__ explicit operator float() const { return hi + lo; }
 };
 
+#if defined(__CUDACC__)
+
 __device__ __forceinline__ df df_two_sum(float a, float b)
 {
     float s = __fadd_rn(a, b);
@@ -111,5 +113,7 @@ __device__ __forceinline__ bool operator<=(df a, df b) { return !(b < a); }
 __device__ __forceinline__ bool operator==(df a, df b) { return a.hi == b.hi && a.lo == b.lo; }
 __device__ __forceinline__ df &operator+=(df &a, df b) { a = a + b; return a; }
 __device__ __forceinline__ df &operator*=(df &a, df b) { a = a * b; return a; }
+
+#endif  // __CUDACC__
 
 }  // namespace gfc

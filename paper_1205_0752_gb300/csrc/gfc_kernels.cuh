@@ -1,0 +1,986 @@
+// Device code of libgfc for sm_103a: Kernel 1 (grid, Step 4) fused into
+// Kernel 2 (the 2-D quadrature per point, Step 5) of Sect. 4 of the paper.
+// Included by gfc_kernels.cu (G0(mu2), grid points, dispatch) and by
+// gfc_eval_inst.cu, which is compiled once per (arithmetic, angular pair
+// count) so that the instantiations build in parallel.
+//
+// Work layout: one warp per point of x (dynamic assignment through an atomic
+// counter); the 32 lanes split the radial nodes of the point's contour; each
+// lane runs the whole angular sum of its node with the angular table held in
+// the kernel's constant bank (fully unrolled), so the inner loop issues no
+// loads. The angular sum is paired (psi, pi - psi) and written in a
+// square-root-free, leading-order-subtracted form:
+//
+//   sum_j w_j (v t_j - 1)/(1 - w t_j)
+//     = (delta y - Omega (x + M2)) / a - Omega1 w + (v - w) w T2,
+//   T2 = sum_j w_j t_j^2 / (1 - w t_j) = A - conj(w) B,
+//   A = sum_j w_j t_j^2 / |1 - w t_j|^2,  B = sum_j w_j t_j^3 / |1 - w t_j|^2,
+//
+// with a = x + y + M2, v = 4y/a, w = 4xy/a^2, t_j = cos^2 psi_j, Omega =
+// sum w_j, Omega1 = sum w_j t_j, delta = 4 Omega1 - Omega. This is the
+// combined-fraction integrand of eq. 20 summed over the symmetric pair; each
+// pair costs one real reciprocal and a handful of FMAs, and A, B are sums of
+// positive terms. The radial sum is compensated (TwoSum) in the binary32 path.
+#pragma once
+
+#include <math.h>
+#include <stdint.h>
+
+#include <type_traits>
+
+#include "gfc_df.h"
+#include "gfc_internal.h"
+
+namespace gfc {
+
+// calibration of the binary32 error estimate (multiple of 2^-24 per unit of
+// the nodes' error scale), from binary32-vs-FP64 runs over the test grids
+constexpr double kMixedErrFactor = 2.0;
+constexpr float kMixedPinchQ = 1e-5f;   // |1 - w t|^2 below which a point is routed
+
+// ----------------------------------------------------------------------------
+// complex arithmetic
+// ----------------------------------------------------------------------------
+template <typename T>
+struct C {
+    T r, i;
+};
+
+template <typename T>
+__device__ __forceinline__ C<T> cx(T r, T i) { return C<T>{r, i}; }
+template <typename T>
+__device__ __forceinline__ C<T> operator+(C<T> a, C<T> b) { return {a.r + b.r, a.i + b.i}; }
+template <typename T>
+__device__ __forceinline__ C<T> operator-(C<T> a, C<T> b) { return {a.r - b.r, a.i - b.i}; }
+template <typename T>
+__device__ __forceinline__ C<T> operator*(C<T> a, C<T> b)
+{
+    return {a.r * b.r - a.i * b.i, a.r * b.i + a.i * b.r};
+}
+template <typename T>
+__device__ __forceinline__ C<T> operator*(T s, C<T> a) { return {s * a.r, s * a.i}; }
+template <typename T>
+__device__ __forceinline__ C<T> conj(C<T> a) { return {a.r, -a.i}; }
+
+__device__ __forceinline__ float rcp(float x)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// 1/x in binary64: hardware seed, then one order-3 Newton-Raphson step,
+// r <- r (1 + e + e^2) with e = 1 - x r (the truncated series of 1/(1 - e)),
+// which takes a seed error e to e^3.
+__device__ __forceinline__ double rcp(double x)
+{
+    double r;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
+    double e = fma(-x, r, 1.0);
+    return fma(r, fma(e, e, e), r);
+}
+
+template <typename T>
+__device__ __forceinline__ C<T> cinv(C<T> a)
+{
+    T n = a.r * a.r + a.i * a.i;
+    T s = rcp(n);
+    return {a.r * s, -a.i * s};
+}
+
+__device__ __forceinline__ float tsqrt(float x) { return sqrtf(x); }
+__device__ __forceinline__ double tsqrt(double x) { return sqrt(x); }
+__device__ __forceinline__ float tatan2(float y, float x) { return atan2f(y, x); }
+__device__ __forceinline__ double tatan2(double y, double x) { return atan2(y, x); }
+
+// principal square root
+template <typename T>
+__device__ __forceinline__ C<T> csqrt_p(C<T> z)
+{
+    T m = tsqrt(z.r * z.r + z.i * z.i);
+    if (m == T(0)) return {T(0), T(0)};
+    if (z.r >= T(0)) {
+        T u = tsqrt(T(0.5) * (m + z.r));
+        return {u, z.i / (T(2) * u)};
+    }
+    T v = tsqrt(T(0.5) * (m - z.r));
+    v = z.i < T(0) ? -v : v;
+    return {z.i / (T(2) * v), v};
+}
+
+template <typename T>
+__device__ __forceinline__ T cabs2(C<T> a) { return a.r * a.r + a.i * a.i; }
+template <typename T>
+__device__ __forceinline__ T cabs1(C<T> a) { return fabs(a.r) + fabs(a.i); }
+
+// ----------------------------------------------------------------------------
+// per-point contour plan (Step 3)
+// ----------------------------------------------------------------------------
+template <typename T>
+struct Term {
+    C<T> c;      // coefficient
+    C<T> m2k;    // k-leg 1/(y + m2k) (ignored when full)
+    C<T> m2q;    // (p-k)-leg mass: a = x + y + m2q
+    int full;    // k-leg is the whole dressed propagator
+};
+
+template <typename T>
+struct Plan {
+    int npass;
+    int kind[2];
+    int nterm[2];
+    Term<T> term[2][2];
+    C<T> eth;    // e^{i arg(x)/2}: direction of the q-ray
+    C<T> yp;     // pole passed by the detour
+};
+
+template <typename T>
+__device__ __forceinline__ C<T> cvt(double r, double i) { return {T(r), T(i)}; }
+
+__device__ __forceinline__ double PI_D() { return 3.14159265358979323846; }
+
+// distance from the y-ray along arg y = phi to the point y0
+__device__ __forceinline__ double ray_distance(double y0r, double y0i, double phi)
+{
+    double d = fabs(atan2(y0i, y0r) - phi);
+    if (d > PI_D()) d = 2.0 * PI_D() - d;
+    return d < 0.5 * PI_D() ? sqrt(y0r * y0r + y0i * y0i) * sin(d) : sqrt(y0r * y0r + y0i * y0i);
+}
+
+// The plan is decided in binary64 (it selects among contours), then its
+// numbers are rounded to T.
+template <typename T>
+__device__ Plan<T> make_plan(const KParams &kp, double xr, double xi)
+{
+    Plan<T> P;
+    const PropConst &pc = kp.pc;
+    double phi = atan2(xi, xr);
+    double ax = sqrt(xr * xr + xi * xi);
+    // e^{i phi/2} as the principal root of x/|x|
+    {
+        C<double> u = ax > 0.0 ? C<double>{xr / ax, xi / ax} : C<double>{1.0, 0.0};
+        C<double> e = csqrt_p(u);
+        P.eth = cvt<T>(e.r, e.i);
+    }
+    P.npass = 1;
+    P.kind[0] = PASS_RAY;
+    P.kind[1] = PASS_RAY;
+    P.nterm[0] = 1;
+    P.nterm[1] = 0;
+    P.yp = {T(0), T(0)};
+    if (pc.kind == 0) {                       // SCALAR
+        Term<T> t;
+        t.c = {T(1), T(0)};
+        t.m2k = t.m2q = {T(pc.m2), T(0)};
+        t.full = 0;
+        P.term[0][0] = t;
+    } else if (pc.kind == 1) {                // CPAIR
+        // k-leg carries the pole in the half-plane of Im x; on the real axis
+        // the legs stay as given (yu_* then holds the given k-leg pole)
+        double ykr = pc.yu_re, yki = xi < 0.0 ? -pc.yu_im : pc.yu_im;
+        if (xi == 0.0) { ykr = pc.yk0_re; yki = pc.yk0_im; }
+        Term<T> t;
+        t.c = {T(1), T(0)};
+        t.m2k = cvt<T>(-ykr, -yki);
+        t.m2q = cvt<T>(-ykr, yki);
+        t.full = 0;
+        P.term[0][0] = t;
+        bool swept = xi != 0.0 && fabs(phi) > pc.arg_yu;
+        bool graze = xi != 0.0 && ray_distance(ykr, yki, phi) < 2.0 * kp.r_detour;
+        if (swept || graze) {
+            P.kind[0] = PASS_DETOUR;
+            P.yp = cvt<T>(ykr, yki);
+        }
+    } else {                                  // DRESSED
+        C<double> yp = {pc.yp_re, pc.yp_im}, ym = {pc.yp_re, -pc.yp_im};
+        C<double> Rp = {pc.Rp_re, pc.Rp_im}, Rm = {pc.Rp_re, -pc.Rp_im};
+        if (fabs(phi) < pc.arg_yp) {
+            // nothing swept: P(y) [P(s) - P(y)] on the ray, P(s) split in two
+            P.nterm[0] = 2;
+            P.term[0][0] = Term<T>{cvt<T>(Rp.r, Rp.i), {T(0), T(0)}, cvt<T>(-yp.r, -yp.i), 1};
+            P.term[0][1] = Term<T>{cvt<T>(Rm.r, Rm.i), {T(0), T(0)}, cvt<T>(-ym.r, -ym.i), 1};
+        } else {
+            // partial fractions: the equal-pole terms on the ray (the one
+            // whose pole lies in the half-plane of Im x on the opposite q-ray,
+            // which flips the sign of the measure when D is odd), the mixed
+            // term on the detour around the pole in the half-plane of Im x
+            double sgn = (kp.dim & 1) ? -1.0 : 1.0;
+            C<double> Rp2 = Rp * Rp, Rm2 = Rm * Rm;
+            double sp = xi > 0.0 ? sgn : 1.0, sm = xi > 0.0 ? 1.0 : sgn;
+            P.nterm[0] = 2;
+            P.term[0][0] = Term<T>{cvt<T>(sp * Rp2.r, sp * Rp2.i), cvt<T>(-yp.r, -yp.i),
+                                   cvt<T>(-yp.r, -yp.i), 0};
+            P.term[0][1] = Term<T>{cvt<T>(sm * Rm2.r, sm * Rm2.i), cvt<T>(-ym.r, -ym.i),
+                                   cvt<T>(-ym.r, -ym.i), 0};
+            C<double> yk = xi > 0.0 ? yp : ym, yq = xi > 0.0 ? ym : yp;
+            C<double> c2 = 2.0 * (Rp * Rm);
+            P.npass = 2;
+            P.kind[1] = PASS_DETOUR;
+            P.nterm[1] = 1;
+            P.term[1][0] = Term<T>{cvt<T>(c2.r, c2.i), cvt<T>(-yk.r, -yk.i),
+                                   cvt<T>(-yq.r, -yq.i), 0};
+            P.yp = cvt<T>(yk.r, yk.i);
+        }
+    }
+    return P;
+}
+
+// Binary64 band of the mixed precision: points whose radial ray runs within
+// pinch_angle of a direction where the angular integrand pinches, or that lie
+// within cut_band of a branch-cut half-line on the real axis.
+__device__ __forceinline__ bool in_band(const KParams &kp, double xr, double xi)
+{
+    const PropConst &pc = kp.pc;
+    double d = xr <= pc.thr ? fabs(xi) : sqrt((xr - pc.thr) * (xr - pc.thr) + xi * xi);
+    if (d < kp.cut_band) return true;
+    if (pc.pinch > 0.0 && fabs(fabs(atan2(xi, xr)) - pc.pinch) < kp.pinch_angle) return true;
+    return false;
+}
+
+// ----------------------------------------------------------------------------
+// nodes of the contour (Step 3) with the measure (1/2) y^((D-2)/2) dy
+// ----------------------------------------------------------------------------
+template <typename T>
+struct Node {
+    C<T> y;
+    C<T> Jt;    // measure / (1 + |y|)^2
+    T sc;       // 1 + |y|
+};
+
+template <typename T>
+__device__ __forceinline__ float2 ld(const float2 *p) { return __ldg(p); }
+
+template <typename T>
+__device__ __forceinline__ void load2(const KParams &kp, int which, int k, T &a, T &b);
+
+template <>
+__device__ __forceinline__ void load2<double>(const KParams &kp, int which, int k, double &a,
+                                              double &b)
+{
+    const double2 *p = which == 0 ? kp.rad64 : (which == 1 ? kp.seg64 : kp.arc64);
+    double2 v = __ldg(p + k);
+    a = v.x;
+    b = v.y;
+}
+
+template <>
+__device__ __forceinline__ void load2<df>(const KParams &kp, int which, int k, df &a, df &b)
+{
+    const float4 *p = which == 0 ? kp.rad_df : (which == 1 ? kp.seg_df : kp.arc_df);
+    float4 v = __ldg(p + k);
+    a = df(v.x, v.y);
+    b = df(v.z, v.w);
+}
+
+template <>
+__device__ __forceinline__ void load2<float>(const KParams &kp, int which, int k, float &a,
+                                             float &b)
+{
+    const float2 *p = which == 0 ? kp.rad32 : (which == 1 ? kp.seg32 : kp.arc32);
+    float2 v = __ldg(p + k);
+    a = v.x;
+    b = v.y;
+}
+
+// q-ray node: q = (rho0 + rho_k) e^{i theta}, measure q^(D-1) dq
+template <typename T>
+__device__ __forceinline__ Node<T> ray_node(const KParams &kp, int k, C<T> eth, C<T> eD, T rho0)
+{
+    T rho, W;
+    load2<T>(kp, 0, k, rho, W);
+    rho += rho0;
+    Node<T> n;
+    C<T> q = rho * eth;
+    n.y = q * q;
+    T r2 = rho * rho;
+    n.sc = T(1) + r2;
+    T s = rcp(n.sc);
+    s = s * s;
+    // q^(D-1) e^{i theta} = rho^(D-1) e^{i D theta};
+    // rho^(D-1) W / (1 + rho^2)^2, scaled first so binary32 cannot overflow
+    T rs = r2 * s;
+    T mag = (kp.dim == 4 ? rs * rho : rs) * W;
+    n.Jt = mag * eD;
+    return n;
+}
+
+template <typename T>
+__device__ __forceinline__ C<T> half_pow(const KParams &kp, C<T> y)
+{
+    // (1/2) y^((D-2)/2): D = 4 -> y/2, D = 3 -> sqrt(y)/2 (principal)
+    if (kp.dim == 4) return T(0.5) * y;
+    return T(0.5) * csqrt_p(y);
+}
+
+template <typename T>
+__device__ __forceinline__ Node<T> finish_y_node(const KParams &kp, C<T> y, C<T> dy)
+{
+    Node<T> n;
+    n.y = y;
+    n.sc = T(1) + tsqrt(cabs2(y));
+    T s = rcp(n.sc);
+    s = s * s;
+    n.Jt = s * (half_pow(kp, y) * dy);
+    return n;
+}
+
+// detour node k of 3 n_s + n_r: q-segment 0 -> q1, half circle around yp,
+// straight segment out to R_d e^{i phi}, ray to infinity from |q| = sqrt(R_d)
+template <typename T>
+__device__ __forceinline__ Node<T> detour_node(const KParams &kp, int k, C<T> eth, C<T> eD,
+                                               C<T> yp, C<T> x)
+{
+    const int ns = kp.n_s;
+    T ap = tsqrt(cabs2(yp));
+    C<T> u = (rcp(ap)) * yp;
+    T r = T(kp.r_detour);
+    T Rd = tsqrt(cabs2(x)) + T(20);
+    if (k >= 3 * ns) return ray_node<T>(kp, k - 3 * ns, eth, eD, tsqrt(Rd));
+    T t, w;
+    if (k < ns) {
+        load2<T>(kp, 1, k, t, w);
+        C<T> q1 = csqrt_p((ap - r) * u);
+        C<T> q = t * q1;
+        Node<T> n;
+        n.y = q * q;
+        n.sc = T(1) + cabs2(q);
+        T s = rcp(n.sc);
+        s = s * s;
+        // measure q^(D-1) dq, dq = q1 w
+        C<T> qd = kp.dim == 4 ? q * q * q : q * q;
+        n.Jt = s * (w * (qd * q1));
+        return n;
+    }
+    if (k < 2 * ns) {
+        load2<T>(kp, 1, k - ns, t, w);
+        T cs, sn;
+        load2<T>(kp, 2, k - ns, cs, sn);
+        // theta = th0 + sg pi t with e^{i th0} = -u, sg = sign(Im yp)
+        T sg = yp.i > T(0) ? T(1) : T(-1);
+        C<T> e = cx<T>(-u.r, -u.i) * cx<T>(cs, sg * sn);
+        C<T> y = yp + r * e;
+        C<T> dy = (sg * T(PI_D()) * r * w) * cx<T>(-e.i, e.r);   // i r e dtheta
+        return finish_y_node<T>(kp, y, dy);
+    }
+    load2<T>(kp, 1, k - 2 * ns, t, w);
+    C<T> y0 = (ap + r) * u;
+    C<T> y1 = Rd * (eth * eth);
+    C<T> d = y1 - y0;
+    return finish_y_node<T>(kp, y0 + t * d, w * d);
+}
+
+// ----------------------------------------------------------------------------
+// angular pair sum
+// ----------------------------------------------------------------------------
+template <typename T, int NT>
+struct Setup {
+    C<T> ia[NT], v[NT], w[NT];
+};
+
+// |1 - w t|^2 for one angular node. Direct form (1 - wr t)^2 + (wi t)^2: its
+// rounding error relative to the result is ~ eps/|1 - w t| next to a pinch.
+// Horner form 1 + t (|w|^2 t - 2 wr): two FMAs, error ~ eps/|1 - w t|^2, used
+// only for compressed rules, whose selection keeps |1 - w t| away from zero.
+__device__ __forceinline__ double q_direct(double t, double wr, double wi)
+{
+    double dr = fma(-wr, t, 1.0);
+    double di = wi * t;
+    return fma(dr, dr, di * di);
+}
+__device__ __forceinline__ float q_direct(float t, float wr, float wi)
+{
+    float dr = fmaf(-wr, t, 1.0f);
+    float di = wi * t;
+    // keep the reciprocal finite if rounding lands on zero at a pinch
+    return fmaxf(fmaf(dr, dr, di * di), 1e-30f);
+}
+__device__ __forceinline__ df q_direct(df t, df wr, df wi)
+{
+    df dr = fma(-wr, t, df(1));
+    df di = wi * t;
+    return fma(dr, dr, di * di);
+}
+template <typename T>
+__device__ __forceinline__ T q_horner(T t, T w2, T m2wr)
+{
+    return fma(fma(w2, t, m2wr), t, T(1));
+}
+
+// Bernstein-ellipse parameter of the pole t = 1/w of 1/(1 - w t) for the
+// interval [0, 1]: rho = |s0 + sqrt(s0 - 1) sqrt(s0 + 1)| >= 1, s0 = 2/w - 1.
+__device__ __forceinline__ float rho_of(float wr, float wi)
+{
+    float n2 = wr * wr + wi * wi;
+    if (!(n2 > 0.0f)) return __int_as_float(0x7f800000);
+    C<float> s0 = {2.0f * wr / n2 - 1.0f, -2.0f * wi / n2};
+    C<float> a = csqrt_p(C<float>{s0.r - 1.0f, s0.i}), b = csqrt_p(C<float>{s0.r + 1.0f, s0.i});
+    C<float> z = s0 + a * b;
+    float m = sqrtf(cabs2(z));
+    return m >= 1.0f ? m : 1.0f / m;
+}
+
+template <typename T>
+__device__ __forceinline__ float rho_min(const KParams &kp, int r);
+template <>
+__device__ __forceinline__ float rho_min<float>(const KParams &kp, int r) { return kp.rho_min32[r]; }
+template <>
+__device__ __forceinline__ float rho_min<double>(const KParams &kp, int r) { return kp.rho_min64[r]; }
+template <>
+__device__ __forceinline__ float rho_min<df>(const KParams &kp, int r) { return kp.rho_min64[r]; }
+
+// one node (tau, gamma, gamma tau) of a compressed rule in shared memory
+__device__ __forceinline__ void rule_node(const void *srules, int k, double &t, double &e,
+                                          double &g)
+{
+    const double *p = reinterpret_cast<const double *>(srules) + 3 * k;
+    t = p[0];
+    e = p[1];
+    g = p[2];
+}
+__device__ __forceinline__ void rule_node(const void *srules, int k, df &t, df &e, df &g)
+{
+    const float2 *p = reinterpret_cast<const float2 *>(srules) + 3 * k;
+    t = df(p[0].x, p[0].y);
+    e = df(p[1].x, p[1].y);
+    g = df(p[2].x, p[2].y);
+}
+__device__ __forceinline__ void rule_node(const void *srules, int k, float &t, float &e, float &g)
+{
+    float4 v = reinterpret_cast<const float4 *>(srules)[k];
+    t = v.x;
+    e = v.y;
+    g = v.z;
+}
+
+// Angular sums A = sum e_j/q_j, B = sum g_j/q_j for NT terms; qmin (binary32
+// only) is the smallest q met, a measure of how close the node is to a pinch.
+template <typename T, int NP, int NT>
+__device__ __forceinline__ int pair_sums(const KParams &kp, const AngTab<T, tab_size<NP>()> &tab,
+                                         int npair, const T *stab, const void *srules,
+                                         const C<T> (&w)[NT], T (&A)[NT], T (&B)[NT], T &qmin)
+{
+    constexpr bool f32 = sizeof(T) == 4;
+    T w2[NT], m2wr[NT], A1[NT], B1[NT];
+#pragma unroll
+    for (int s = 0; s < NT; ++s) {
+        w2[s] = cabs2(w[s]);
+        m2wr[s] = T(-2) * w[s].r;
+        A[s] = B[s] = A1[s] = B1[s] = T(0);
+    }
+    T qm = T(1e30);
+    // the smallest compressed rule that is exact to rounding level for every
+    // term, made uniform over the lanes that run together
+    int rule = kp.nrule;
+    {
+        float rho = __int_as_float(0x7f800000);
+#pragma unroll
+        for (int s = 0; s < NT; ++s) rho = fminf(rho, rho_of((float)w[s].r, (float)w[s].i));
+        for (int q = 0; q < kp.nrule; ++q)
+            if (rho >= rho_min<T>(kp, q)) {
+                rule = q;
+                break;
+            }
+        rule = __reduce_max_sync(__activemask(), rule);
+    }
+    if (rule < kp.nrule) {
+        const int off = kp.rule_off[rule], n = kp.rule_n[rule];
+#pragma unroll 4
+        for (int k = 0; k < n; ++k) {
+            T t, e, g;
+            rule_node(srules, off + k, t, e, g);
+#pragma unroll
+            for (int s = 0; s < NT; ++s) {
+                T q = f32 ? q_direct(t, w[s].r, w[s].i) : q_horner(t, w2[s], m2wr[s]);
+                if (f32) qm = fmin(qm, q);
+                T r = rcp(q);
+                A[s] = fma(e, r, A[s]);
+                B[s] = fma(g, r, B[s]);
+            }
+        }
+    } else if (NP > 0) {
+#pragma unroll
+        for (int j = 0; j < NP; ++j) {
+            const T t = tab.t[j], e = tab.e[j], g = tab.g[j];
+#pragma unroll
+            for (int s = 0; s < NT; ++s) {
+                T q = q_direct(t, w[s].r, w[s].i);
+                if (f32) qm = fmin(qm, q);
+                T r = rcp(q);
+                if (j & 1) {
+                    A1[s] = fma(e, r, A1[s]);
+                    B1[s] = fma(g, r, B1[s]);
+                } else {
+                    A[s] = fma(e, r, A[s]);
+                    B[s] = fma(g, r, B[s]);
+                }
+            }
+        }
+    } else {
+#pragma unroll 4
+        for (int j = 0; j < npair; ++j) {
+            const T t = stab[3 * j], e = stab[3 * j + 1], g = stab[3 * j + 2];
+#pragma unroll
+            for (int s = 0; s < NT; ++s) {
+                T q = q_direct(t, w[s].r, w[s].i);
+                if (f32) qm = fmin(qm, q);
+                T r = rcp(q);
+                A[s] = fma(e, r, A[s]);
+                B[s] = fma(g, r, B[s]);
+            }
+        }
+    }
+#pragma unroll
+    for (int s = 0; s < NT; ++s) {
+        A[s] += A1[s];
+        B[s] += B1[s];
+    }
+    qmin = qm;
+    return rule < kp.nrule ? kp.rule_n[rule] : npair;
+}
+
+// Per-pass constants of one point, computed once and reused for every node.
+template <typename T, int NT>
+struct PassPre {
+    int nt;
+    C<T> m2q[NT], m2k[NT];
+    C<T> cx2[NT];     // c_t 2x
+    C<T> omx[NT];     // Omega (x + M2_t)
+    int full[NT];     // k-leg is the whole dressed propagator
+    int same[NT];     // k-leg and (p-k)-leg share the pole: one reciprocal
+};
+
+template <typename T, int NT>
+__device__ __forceinline__ PassPre<T, NT> pass_pre(const KParams &kp, const Plan<T> &P, int pass,
+                                                   C<T> x)
+{
+    PassPre<T, NT> pp;
+    pp.nt = P.nterm[pass];
+    const T Om = T(kp.Omega);
+#pragma unroll
+    for (int s = 0; s < NT; ++s) {
+        const Term<T> &tm = P.term[pass][s < pp.nt ? s : 0];
+        pp.m2q[s] = tm.m2q;
+        pp.m2k[s] = tm.m2k;
+        pp.cx2[s] = tm.c * (T(2) * x);
+        pp.omx[s] = Om * (x + tm.m2q);
+        pp.full[s] = tm.full;
+        pp.same[s] = !tm.full && tm.m2k.r == tm.m2q.r && tm.m2k.i == tm.m2q.i;
+    }
+    return pp;
+}
+
+// Contribution of one node of one pass: Jt * sum_t c_t P1_t(y)/(y + M2_t) *
+// 2x/a_t * S_t, with the (1 + |y|)^2 scale moved from Jt onto the fractions.
+// `mag` receives the node's error scale (binary32 and cond output only) and
+// `qmin` the smallest |1 - w t|^2 of its angular sums (binary32).
+template <typename T, int NP, int NT>
+__device__ __forceinline__ C<T> node_value(const KParams &kp, const AngTab<T, tab_size<NP>()> &tab,
+                                           const T *stab, const void *srules,
+                                           const PassPre<T, NT> &pp, C<T> x, const Node<T> &nd,
+                                           T &mag, T &qmin, int &npairs)
+{
+    C<T> ia[NT], v[NT], w[NT];
+#pragma unroll
+    for (int s = 0; s < NT; ++s) {
+        C<T> a = x + nd.y + pp.m2q[s];
+        ia[s] = cinv(a);
+        v[s] = T(4) * (nd.y * ia[s]);
+        w[s] = (x * v[s]) * ia[s];
+    }
+    T A[NT], B[NT];
+    npairs = pair_sums<T, NP, NT>(kp, tab, kp.npair, stab, srules, w, A, B, qmin) * pp.nt;
+    const T Om1 = T(kp.Omega1), del = T(kp.delta);
+    const bool want_mag = sizeof(T) == 4 || kp.cond_out != nullptr;
+    C<T> sum = {T(0), T(0)};
+    mag = T(0);
+#pragma unroll
+    for (int s = 0; s < NT; ++s) {
+        if (s >= pp.nt) break;
+        C<T> T2 = {A[s] - w[s].r * B[s], w[s].i * B[s]};
+        C<T> lead = (del * nd.y - pp.omx[s]) * ia[s] - Om1 * w[s];
+        C<T> vw = (v[s] - w[s]) * w[s];
+        C<T> S = lead + vw * T2;
+        // (1 + |y|)^2 P1(y) / (y + M2)
+        C<T> pq = nd.sc * cinv(nd.y + pp.m2q[s]);
+        C<T> p1;
+        if (pp.same[s]) {
+            p1 = pq;
+        } else if (pp.full[s]) {
+            C<T> yp = cvt<T>(kp.pc.yp_re, kp.pc.yp_im);
+            C<T> Rp = cvt<T>(kp.pc.Rp_re, kp.pc.Rp_im);
+            p1 = nd.sc * (Rp * cinv(nd.y - yp) + conj(Rp) * cinv(nd.y - conj(yp)));
+        } else {
+            p1 = nd.sc * cinv(nd.y + pp.m2k[s]);
+        }
+        C<T> f = (pp.cx2[s] * (p1 * pq)) * ia[s];
+        sum = sum + f * S;
+        if (want_mag) {
+            // rounding scale of S: its parts without cancellation; A and B are
+            // positive sums that carry the sensitivity to w and to each q
+            T Sabs = cabs1(lead) + cabs1(vw) * (A[s] + cabs1(w[s]) * B[s]);
+            mag += cabs1(f) * Sabs;
+        }
+    }
+    if (want_mag) mag *= cabs1(nd.Jt);
+    return nd.Jt * sum;
+}
+
+// ----------------------------------------------------------------------------
+// compensated accumulation
+// ----------------------------------------------------------------------------
+template <typename T>
+struct Acc {
+    T sr, cr, si, ci;
+    __device__ __forceinline__ void init() { sr = cr = si = ci = T(0); }
+};
+
+// TwoSum (Knuth) on each component: s + v = t + err exactly
+template <typename T>
+__device__ __forceinline__ void two_sum_add(T &s, T &c, T v)
+{
+    T t = s + v;
+    T bp = t - s;
+    T err = (s - (t - bp)) + (v - bp);
+    s = t;
+    c += err;
+}
+
+// binary32: compensated (TwoSum) radial sums; binary64: plain sums (at most
+// n_r/32 terms per lane, error far below the FP64 tolerance)
+__device__ __forceinline__ void acc_add(Acc<float> &a, C<float> v)
+{
+    two_sum_add(a.sr, a.cr, v.r);
+    two_sum_add(a.si, a.ci, v.i);
+}
+__device__ __forceinline__ void acc_add(Acc<double> &a, C<double> v)
+{
+    a.sr += v.r;
+    a.si += v.i;
+}
+__device__ __forceinline__ void acc_add(Acc<df> &a, C<df> v)
+{
+    a.sr = a.sr + v.r;
+    a.si = a.si + v.i;
+}
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// ----------------------------------------------------------------------------
+// the evaluation kernel
+// ----------------------------------------------------------------------------
+__device__ __forceinline__ void point_x(const KParams &kp, int64_t p, double &xr, double &xi)
+{
+    if (kp.use_grid) {
+        // re0 + (i + 1/2) dre with separate roundings (no FMA), as written
+        int i = (int)(p / kp.gn), j = (int)(p - (int64_t)i * kp.gn);
+        xr = __dadd_rn(kp.re0, __dmul_rn(i + 0.5, kp.dre));
+        xi = __dadd_rn(kp.im0, __dmul_rn(j + 0.5, kp.dim_im));
+    } else {
+        xr = kp.x[2 * p];
+        xi = kp.x[2 * p + 1];
+    }
+}
+
+// One pass of a point's contour, the lane's share of its nodes.
+template <typename T, int NP, int NTT>
+__device__ __forceinline__ void run_pass(const KParams &kp, const AngTab<T, tab_size<NP>()> &tab,
+                                         const T *stab, const void *srules, const Plan<T> &P,
+                                         int pass, C<T> x, C<T> eD, int lane, Acc<T> &acc,
+                                         T &amag, T &qall, int &pairs)
+{
+    const PassPre<T, NTT> pp = pass_pre<T, NTT>(kp, P, pass, x);
+    const bool ray = P.kind[pass] == PASS_RAY;
+    const int nn = ray ? kp.n_r : 3 * kp.n_s + kp.n_r;
+    for (int k = lane; k < nn; k += 32) {
+        Node<T> nd = ray ? ray_node<T>(kp, k, P.eth, eD, T(0))
+                         : detour_node<T>(kp, k, P.eth, eD, P.yp, x);
+        T mag, qm;
+        int np;
+        C<T> v = node_value<T, NP, NTT>(kp, tab, stab, srules, pp, x, nd, mag, qm, np);
+        acc_add(acc, v);
+        amag += mag;
+        qall = fmin(qall, qm);
+        pairs += np;
+    }
+}
+
+// Sum over one point's contour, per lane, into acc; returns the point's
+// number of contour nodes.
+template <typename T, int NP, int NT>
+__device__ __forceinline__ int point_sum(const KParams &kp, const AngTab<T, tab_size<NP>()> &tab,
+                                         const T *stab, const void *srules, double xr, double xi,
+                                         int lane, Acc<T> &acc, T &amag, T &qall, int &pairs)
+{
+    const Plan<T> P = make_plan<T>(kp, xr, xi);
+    const C<T> x = cvt<T>(xr, xi);
+    // e^{i D theta} of the ray, once per point
+    const C<T> e2 = P.eth * P.eth;
+    const C<T> eD = kp.dim == 4 ? e2 * e2 : e2 * P.eth;
+    int total = 0;
+#pragma unroll
+    for (int pass = 0; pass < 2; ++pass) {
+        if (pass >= P.npass) break;
+        total += P.kind[pass] == PASS_RAY ? kp.n_r : 3 * kp.n_s + kp.n_r;
+        if (NT > 1 && P.nterm[pass] == 2)
+            run_pass<T, NP, (NT > 1 ? 2 : 1)>(kp, tab, stab, srules, P, pass, x, eD, lane, acc,
+                                             amag, qall, pairs);
+        else
+            run_pass<T, NP, 1>(kp, tab, stab, srules, P, pass, x, eD, lane, acc, amag, qall, pairs);
+    }
+    return total;
+}
+
+__device__ __forceinline__ void list_append(const KParams &kp, int64_t p)
+{
+    unsigned long long k = atomicAdd(kp.list_count, 1ULL);
+    kp.list[k] = p;
+}
+
+// Evaluates point p of the request described by kp under `mode`; the whole
+// warp calls it with the same p.
+template <typename T, int NP, int NT>
+__device__ __forceinline__ void eval_point(const KParams &kp, const AngTab<T, tab_size<NP>()> &tab,
+                                           const T *stab, const void *srules, int64_t p, int mode,
+                                           int lane)
+{
+    double xr, xi;
+    point_x(kp, p, xr, xi);
+    double *out = kp.G + 2 * p;
+    if (xi == 0.0 && (xr < 0.0 || xr == kp.mu2)) {
+        // the cut side of the real axis is undefined (NaN); G(mu2) = 0 by
+        // the subtraction
+        if (mode != MODE_LIST64 && lane == 0) {
+            double v = xr < 0.0 ? __longlong_as_double(0x7ff8000000000000ULL) : 0.0;
+            out[0] = v;
+            out[1] = v;
+            if (kp.cond_out) kp.cond_out[p] = 0.0;
+        }
+        return;
+    }
+    if (mode == MODE_BULK32 && in_band(kp, xr, xi)) {
+        if (lane == 0) list_append(kp, p);
+        return;
+    }
+    Acc<T> acc;
+    acc.init();
+    T amag = T(0), qall = T(1e30);
+    int pairs = 0;
+    int nodes = point_sum<T, NP, NT>(kp, tab, stab, srules, xr, xi, lane, acc, amag, qall, pairs);
+    if (kp.node_count && lane == 0)
+        atomicAdd(kp.node_count, (unsigned long long)nodes * (unsigned long long)(2 * kp.npair));
+    if (kp.pair_count) {
+        unsigned long long pw = (unsigned long long)pairs;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) pw += __shfl_xor_sync(0xffffffffu, pw, o);
+        if (lane == 0) atomicAdd(kp.pair_count, pw);
+    }
+    double sr = warp_sum((double)acc.sr + (double)acc.cr);
+    double si = warp_sum((double)acc.si + (double)acc.ci);
+    double cond = kp.K_D * warp_sum((double)amag);
+    float qpt = (float)qall;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) qpt = fminf(qpt, __shfl_xor_sync(0xffffffffu, qpt, o));
+    if (lane == 0) {
+        double gr = kp.K_D * sr - kp.g0mu[0], gi = kp.K_D * si - kp.g0mu[1];
+        out[0] = gr;
+        out[1] = gi;
+        if (kp.cond_out) kp.cond_out[p] = cond;
+        if (mode == MODE_BULK32 && kp.mixed_rtol > 0.0) {
+            // rounding error of the binary32 sum: a small multiple of 2^-24
+            // times the nodes' error scales. Next to a pinch (some node with
+            // |1 - w t| < 3e-3) the discrete sum is so sensitive to the
+            // binary32 rounding of x and of the nodes that no such bound
+            // holds; those points go to binary64 too.
+            double est = kMixedErrFactor * 5.9604644775390625e-8 * cond;
+            if (!(est <= kp.mixed_rtol * sqrt(gr * gr + gi * gi)) || qpt < kMixedPinchQ)
+                list_append(kp, p);
+        }
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ const void *rules_of(const KParams &kp);
+template <>
+__device__ __forceinline__ const void *rules_of<double>(const KParams &kp) { return kp.rules64; }
+template <>
+__device__ __forceinline__ const void *rules_of<float>(const KParams &kp) { return kp.rules32; }
+template <>
+__device__ __forceinline__ const void *rules_of<df>(const KParams &kp) { return kp.rules_df; }
+
+template <typename T>
+__host__ __device__ constexpr int rule_bytes() { return sizeof(T) == 8 ? 24 : 16; }   // double, df: 3 x 8
+
+// bytes of shared memory: the full pair table (generic kernels only), 16-byte
+// aligned, then the compressed rules
+template <typename T, int NP>
+__host__ __device__ inline size_t smem_bytes(int npair, int rules_total)
+{
+    size_t a = NP > 0 ? 0 : ((sizeof(T) * 3 * npair + 15) / 16) * 16;
+    return a + (size_t)rule_bytes<T>() * rules_total;
+}
+
+// Copies the pair table (NP = 0) and the compressed rules of kp to shared
+// memory; every request of one launch shares them.
+template <typename T, int NP>
+__device__ __forceinline__ void stage_tables(const KParams &kp, const T *gtab, int npair,
+                                             const T *&stab, const void *&srules)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *st = reinterpret_cast<T *>(smem_raw);
+    size_t a = NP > 0 ? 0 : ((sizeof(T) * 3 * npair + 15) / 16) * 16;
+    if (NP == 0)
+        for (int i = threadIdx.x; i < 3 * npair; i += blockDim.x) st[i] = gtab[i];
+    const int nw = rule_bytes<T>() * kp.rules_total / 4;
+    const unsigned *src = reinterpret_cast<const unsigned *>(rules_of<T>(kp));
+    unsigned *dst = reinterpret_cast<unsigned *>(smem_raw + a);
+    for (int i = threadIdx.x; i < nw; i += blockDim.x) dst[i] = src[i];
+    __syncthreads();
+    stab = st;
+    srules = smem_raw + a;
+}
+
+// One request: warps take points from an atomic counter until none is left.
+template <typename T, int NP, int NT>
+__global__ void __launch_bounds__(256)
+eval_kernel(const __grid_constant__ KParams kp,
+            const __grid_constant__ AngTab<T, tab_size<NP>()> tab, const T *__restrict__ gtab)
+{
+    const T *stab;
+    const void *srules;
+    stage_tables<T, NP>(kp, gtab, kp.npair, stab, srules);
+    const int lane = threadIdx.x & 31;
+    const unsigned long long n =
+        kp.mode == MODE_LIST64 ? *kp.list_count : (unsigned long long)kp.npts;
+    for (;;) {
+        unsigned long long p = 0;
+        if (lane == 0) p = atomicAdd(kp.counter, 1ULL);
+        p = __shfl_sync(0xffffffffu, p, 0);
+        if (p >= n) break;
+        int64_t pt = kp.mode == MODE_LIST64 ? kp.list[p] : (int64_t)p;
+        eval_point<T, NP, NT>(kp, tab, stab, srules, pt, kp.mode, lane);
+    }
+}
+
+// Many requests in one persistent launch (continuous batching): item i covers
+// points [items[i].p0, items[i].p1) of request slot items[i].slot; offs[i] is
+// its first index in the launch-wide point count. All requests of a launch
+// share the angular rule (n_angular, D) held in the constant bank.
+template <typename T, int NP, int NT>
+__global__ void __launch_bounds__(256)
+eval_batch_kernel(const KParams *__restrict__ slots, const BatchItem *__restrict__ items,
+                  const int64_t *__restrict__ offs, int nitems, int64_t total,
+                  unsigned long long *counter, int mode,
+                  const __grid_constant__ AngTab<T, tab_size<NP>()> tab, const T *__restrict__ gtab,
+                  int npair)
+{
+    const T *stab;
+    const void *srules;
+    stage_tables<T, NP>(slots[items[0].slot], gtab, npair, stab, srules);
+    const int lane = threadIdx.x & 31;
+    for (;;) {
+        unsigned long long p = 0;
+        if (lane == 0) p = atomicAdd(counter, 1ULL);
+        p = __shfl_sync(0xffffffffu, p, 0);
+        if (p >= (unsigned long long)total) break;
+        int lo = 0, hi = nitems - 1;
+        while (lo < hi) {
+            int mid = (lo + hi + 1) >> 1;
+            if (offs[mid] <= (int64_t)p) lo = mid;
+            else hi = mid - 1;
+        }
+        const BatchItem it = items[lo];
+        const KParams &kp = slots[it.slot];
+        int64_t q = it.p0 + ((int64_t)p - offs[lo]);
+        eval_point<T, NP, NT>(kp, tab, stab, srules, mode == MODE_LIST64 ? kp.list[q] : q, mode,
+                              lane);
+    }
+}
+
+// ----------------------------------------------------------------------------
+// host launchers
+// ----------------------------------------------------------------------------
+static inline int sm_count()
+{
+    static int n = 0;
+    if (n == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (n <= 0) n = 1;
+    }
+    return n;
+}
+
+template <typename T, int NP>
+static void fill_tab(AngTab<T, NP> &tab, const DevTables &tb, int npair)
+{
+    for (int j = 0; j < NP; ++j) {
+        tab.t[j] = j < npair ? T(tb.t[j]) : T(0);
+        tab.e[j] = j < npair ? T(tb.e[j]) : T(0);
+        tab.g[j] = j < npair ? T(tb.g[j]) : T(0);
+    }
+}
+
+template <typename T>
+const T *gtab_of(const DevTables &tb);
+template <>
+inline const double *gtab_of<double>(const DevTables &tb) { return tb.ang64; }
+template <>
+inline const float *gtab_of<float>(const DevTables &tb) { return tb.ang32; }
+template <>
+inline const df *gtab_of<df>(const DevTables &tb) { return reinterpret_cast<const df *>(tb.ang_df); }
+
+template <typename T, int NP, int NT>
+static cudaError_t run_eval(const KParams &kp, const DevTables &tb, cudaStream_t st)
+{
+    AngTab<T, tab_size<NP>()> tab;
+    fill_tab(tab, tb, NP > 0 ? kp.npair : 0);
+    size_t smem = smem_bytes<T, NP>(kp.npair, kp.rules_total);
+    int blocks_per_sm = 0;
+    cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &blocks_per_sm, (const void *)eval_kernel<T, NP, NT>, 256, smem);
+    if (err != cudaSuccess) return err;
+    if (blocks_per_sm < 1) blocks_per_sm = 1;
+    int64_t blocks = (kp.npts + 7) / 8;
+    int64_t cap = (int64_t)sm_count() * blocks_per_sm;
+    if (blocks > cap) blocks = cap;
+    if (blocks < 1) blocks = 1;
+    eval_kernel<T, NP, NT><<<(unsigned)blocks, 256, smem, st>>>(kp, tab, gtab_of<T>(tb));
+    return cudaGetLastError();
+}
+
+template <typename T, int NP, int NT>
+static cudaError_t run_batch(const BatchLaunch &bl, const DevTables &tb, cudaStream_t st)
+{
+    AngTab<T, tab_size<NP>()> tab;
+    fill_tab(tab, tb, NP > 0 ? bl.npair : 0);
+    size_t smem = smem_bytes<T, NP>(bl.npair, bl.rules_total);
+    int blocks_per_sm = 0;
+    cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &blocks_per_sm, (const void *)eval_batch_kernel<T, NP, NT>, 256, smem);
+    if (err != cudaSuccess) return err;
+    if (blocks_per_sm < 1) blocks_per_sm = 1;
+    int64_t blocks = (bl.total + 7) / 8;
+    int64_t cap = (int64_t)sm_count() * blocks_per_sm;
+    if (blocks > cap) blocks = cap;
+    if (blocks < 1) blocks = 1;
+    eval_batch_kernel<T, NP, NT><<<(unsigned)blocks, 256, smem, st>>>(
+        bl.slots, bl.items, bl.offs, bl.nitems, bl.total, bl.counter, bl.mode, tab,
+        gtab_of<T>(tb), bl.npair);
+    return cudaGetLastError();
+}
+
+// One launch of the evaluation kernel (one request) or of the batched kernel
+// (many requests), binary arithmetic T, pair table unrolled for NP pairs (0:
+// generic loop). Defined in gfc_eval_inst.cu, one object file per (T, NP).
+template <typename T, int NP>
+cudaError_t eval_inst(const KParams &kp, const DevTables &tb, cudaStream_t st);
+template <typename T, int NP>
+cudaError_t batch_inst(const BatchLaunch &bl, const DevTables &tb, bool two_terms, cudaStream_t st);
+
+}  // namespace gfc

@@ -39,7 +39,7 @@ constexpr size_t kOffAng = kOffArc + align256(sizeof(double2) * (kNaMaxRadial / 
 constexpr size_t kOffPart = kOffAng + align256(sizeof(double) * 3 * (kNaMaxAngular / 2));
 constexpr size_t kOffG0 = kOffPart + align256(sizeof(double) * 2 * kNaMaxG0Warps);
 constexpr size_t kOffCnt = kOffG0 + align256(sizeof(double) * 2);
-constexpr size_t kOffTicket = kOffCnt + align256(sizeof(unsigned long long) * 4);
+constexpr size_t kOffTicket = kOffCnt + align256(sizeof(unsigned long long) * kCounters);
 constexpr size_t kNoAllocBytes = kOffTicket + align256(sizeof(unsigned));
 
 }  // namespace

@@ -45,12 +45,13 @@ constexpr int kG0Warps = 512;
 // work per launch in units of binary32 pair evaluations (about 20-40 ms)
 constexpr double kLaunchWork = 1.5e11;
 constexpr double kFp64Weight = 24.0; // binary64 pair cost in binary32 pair units
+constexpr double kDfWeight = 6.0;    // double-float pair cost in binary32 pair units
 
 enum ReqState { R_QUEUED, R_ACTIVE, R_COPYING, R_DONE };
 
 struct Phase {
     int mode;          // LaunchMode
-    bool fp32;
+    int arith;         // Arith
     int64_t next;      // first point (or list entry) not yet put in an item
     int64_t end;       // points (or list entries) of the phase; -1: not known yet
     int64_t items_out; // items launched and not finished
@@ -93,7 +94,7 @@ struct LaunchRec {
     int64_t *offs_host = nullptr;       // pinned
 };
 
-using GroupKey = std::tuple<int, int, int, int, int>;   // fp32, npair, dim, two, mode
+using GroupKey = std::tuple<int, int, int, int, int>;   // arith, npair, dim, two, mode
 
 }  // namespace
 
@@ -166,13 +167,13 @@ void pinned_put(gfc_server *s, void *p, size_t n)
     if (p) s->pinned_free.push_back({p, n});
 }
 
-double work_per_point(const Request &r, bool fp32)
+double work_per_point(const Request &r, int arith)
 {
     double nodes = r.params.n_radial;
     if (r.prop.kind != GFC_PROP_SCALAR) nodes *= 1.75;
     double terms = r.prop.kind == GFC_PROP_DRESSED ? 2.0 : 1.0;
     double w = nodes * (r.params.n_angular / 2) * terms;
-    return fp32 ? w : w * kFp64Weight;
+    return arith == ARITH_F32 ? w : (arith == ARITH_DF ? w * kDfWeight : w * kFp64Weight);
 }
 
 void release_request(gfc_server *s, Request *r)
@@ -262,9 +263,11 @@ int admit(gfc_server *s, Request *r)
     if (e != cudaSuccess) return cuda_fail(e, "g0mu launch");
     cudaEventRecord(s->admit_event, s->admit_stream);
     if (!mixed) {
-        r->phases = {Phase{MODE_ALL, false, 0, r->npts, 0}};
+        int ar = r->params.precision == GFC_F32X2 ? ARITH_DF : ARITH_F64;
+        r->phases = {Phase{MODE_ALL, ar, 0, r->npts, 0}};
     } else {
-        r->phases = {Phase{MODE_BULK32, true, 0, r->npts, 0}, Phase{MODE_LIST64, false, 0, -1, 0}};
+        int ar = r->params.mixed_fallback == GFC_F32X2 ? ARITH_DF : ARITH_F64;
+        r->phases = {Phase{MODE_BULK32, ARITH_F32, 0, r->npts, 0}, Phase{MODE_LIST64, ar, 0, -1, 0}};
     }
     r->state = R_ACTIVE;
     s->active.push_back(r);
@@ -287,7 +290,7 @@ void issue_launches(gfc_server *s)
         for (int p = 0; p < (int)r->phases.size(); ++p) {
             const Phase &ph = r->phases[p];
             if (ph.end < 0 || ph.next >= ph.end) continue;
-            GroupKey k{ph.fp32 ? 1 : 0, r->params.n_angular / 2, r->params.dim,
+            GroupKey k{ph.arith, r->params.n_angular / 2, r->params.dim,
                        r->prop.kind == GFC_PROP_DRESSED ? 1 : 0, ph.mode};
             groups[k].push_back({r, p});
         }
@@ -302,7 +305,7 @@ void issue_launches(gfc_server *s)
         if (li < 0) return;
         LaunchRec &L = s->ring[li];
         const GroupKey &key = kv.first;
-        const bool fp32 = std::get<0>(key) != 0;
+        const int arith = std::get<0>(key);
         const int mode = std::get<4>(key);
         auto &members = kv.second;
         // round-robin over the group's requests, each item bounded so that no
@@ -319,7 +322,7 @@ void issue_launches(gfc_server *s)
                 Request *r = m.first;
                 Phase &ph = r->phases[m.second];
                 if (ph.next >= ph.end || nitems >= kMaxItems || budget <= 0) continue;
-                double wpp = work_per_point(*r, fp32);
+                double wpp = work_per_point(*r, arith);
                 double share = std::max(budget / members.size(), wpp * 256.0);
                 int64_t n = (int64_t)std::max(1.0, share / wpp);
                 n = std::min(n, ph.end - ph.next);
@@ -357,7 +360,7 @@ void issue_launches(gfc_server *s)
         bl.npair = std::get<1>(key);
         Request *r0 = members.front().first;
         bl.rules_total = r0->kp.rules_total;
-        cudaError_t e = launch_batch(bl, dev_tables_c(*r0->T), fp32, std::get<3>(key) != 0, st);
+        cudaError_t e = launch_batch(bl, dev_tables_c(*r0->T), arith, std::get<3>(key) != 0, st);
         if (e != cudaSuccess) {
             s->error = GFC_ECUDA;
         }
@@ -511,7 +514,7 @@ int gfc_server_create(int device, size_t hbm_budget_bytes, int max_slots, gfc_se
          cudaMalloc((void **)&s->partials_dev, sizeof(double) * 2 * kG0Warps) == cudaSuccess &&
          cudaMalloc((void **)&s->ticket_dev, sizeof(unsigned)) == cudaSuccess &&
          cudaMemset(s->ticket_dev, 0, sizeof(unsigned)) == cudaSuccess &&
-         cudaMalloc((void **)&s->dummy_counters, sizeof(unsigned long long) * 4) == cudaSuccess;
+         cudaMalloc((void **)&s->dummy_counters, sizeof(unsigned long long) * kCounters) == cudaSuccess;
     for (int i = 0; i < kRing && ok; ++i) {
         LaunchRec &L = s->ring[i];
         ok = cudaEventCreateWithFlags(&L.done, cudaEventDisableTiming) == cudaSuccess &&

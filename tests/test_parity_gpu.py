@@ -19,7 +19,7 @@ if not torch.cuda.is_available():
 
 import paper_1205_0752_gb300 as gfc  # noqa: E402
 
-RTOL = {"fp64": 1e-10, "mixed": 1e-6}
+RTOL = {"fp64": 1e-10, "mixed": 1e-6, "f32x2": 1e-10}
 
 
 def rel_err(G, ref, floor_frac=1e-3):
@@ -60,7 +60,7 @@ def test_grid_points_bit_exact():
         assert np.array_equal(x.cpu().numpy().ravel(), xo)
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("precision", ["fp64", "mixed", "f32x2"])
 def test_bubble_64x64_grid(precision):
     """The 64 x 64 bubble grid (m = 1, D = 4, mu2 = 1, 256 x 64 nodes)."""
     rect = si.grid_rect("small")
@@ -71,7 +71,7 @@ def test_bubble_64x64_grid(precision):
     assert_parity(G, ref, RTOL[precision], x, f"bubble 64x64 {precision}")
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("precision", ["fp64", "mixed", "f32x2"])
 def test_paper_worked_example_grid(precision):
     """Sect. 5: 128 x 128 over [-5,5]^2, masses -+ i/2, x = 0 subtraction,
     64 nodes per sub-contour and 64 angular nodes."""
@@ -84,7 +84,7 @@ def test_paper_worked_example_grid(precision):
 
 
 @pytest.mark.parametrize("dim", [3, 4])
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("precision", ["fp64", "mixed", "f32x2"])
 def test_dressed_grid(dim, precision):
     """Dressed propagator, a seeded (a, b, c) draw, ragged 48 x 40 grid."""
     a, b, c = si.dressed_draws(3, 1)[0]
@@ -168,7 +168,7 @@ def test_row_shards_equal_unsharded():
     assert np.array_equal(np.concatenate(parts), whole)
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("precision", ["fp64", "mixed", "f32x2"])
 @pytest.mark.parametrize("m2", [0.25, 1.0, 4.0])
 def test_production_grid_sampled(precision, m2):
     """1024 x 1024 over [-10,5] x [-5,5], 2048 x 256 nodes (the launch the
@@ -183,7 +183,7 @@ def test_production_grid_sampled(precision, m2):
     assert_parity(G[idx], ref, RTOL[precision], x, f"production m2={m2} {precision}")
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("precision", ["fp64", "mixed", "f32x2"])
 @pytest.mark.parametrize("dim", [3, 4])
 def test_dressed_full_size_sampled(precision, dim):
     """The dressed workload at full size: 512 x 512 over [-8,4] x [-4,4],
@@ -197,3 +197,18 @@ def test_dressed_full_size_sampled(precision, dim):
         x = oracle.grid_points(*rect, 512, 512)[idx]
         ref = oracle.eval_points(prop, oracle_params(par), x)
         assert_parity(G[idx], ref, RTOL[precision], x, f"dressed 512^2 D={dim} draw {k} {precision}")
+
+
+@pytest.mark.parametrize("kind", ["bubble", "paper"])
+def test_mixed_with_double_float_fallback(kind):
+    """Mixed precision whose routed points go to the double-float kernel."""
+    if kind == "bubble":
+        prop, rect, m, n, mu2 = SCALAR, si.grid_rect("small"), 64, 64, 1.0
+    else:
+        prop, rect, m, n, mu2 = PAPER, si.grid_rect("paper"), 128, 128, 0.0
+    par = dict(dim=4, mu2=mu2, n_radial=256, n_angular=64, precision="mixed",
+               mixed_fallback="f32x2")
+    G = run_grid(prop, par, rect, m, n)
+    x = oracle.grid_points(*rect, m, n)
+    ref = oracle.eval_points(prop, oracle_params(par), x)
+    assert_parity(G, ref, RTOL["mixed"], x, f"mixed/f32x2 {kind}")
