@@ -38,6 +38,9 @@ SIDE = 1024
 MASSES2 = (0.25, 1.0, 4.0)          # m in {0.5, 1, 2}
 NR, NA = 2048, 256
 FLOP_PER_NODE_EVAL = 11              # 22 flops per +-psi pair (9 FMA + 4 MUL)
+# DRAM bytes per point of the FP64 evaluation kernel (ncu, one 256x256 launch of the
+# current kernel: 291,328 B read, 0 B written back before the launch ended)
+TRAFFIC_PER_POINT = 291328 / 65536
 SM_COUNT = 152
 SM_MAX_MHZ = 2070.0
 FP64_FMA_PER_SM_CLK = 2              # nominal GB300 FP64 rate (1.25 TFLOP/s)
@@ -361,17 +364,22 @@ def run_gfc(args):
         "gpu_launches": 2 * 3 * args.steps,
         "roofline": {"bound": "alu", "kernel": "eval_kernel<double,128,1>",
                      "achieved": achieved, "peak": peak64, "unit": "TFLOP/s",
-                     "frac": achieved / peak64, "traffic": None,
+                     "frac": achieved / peak64, "traffic": TRAFFIC_PER_POINT * side * side,
+                     "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one "
+                                       "256x256 launch (291,328 B), scaled by points per launch",
                      "peak_source": "derived: 152 SM x 2 FP64 FMA/clk x 2 flop x 2070 MHz "
                                     "(ncu: dfma peak_sustained 304/clk = 152 x 2)",
                      "algorithmic": "11 flop per node-eval (22 per +-psi pair)",
                      "executed_pairs_per_launch": st64.pairs_evaluated,
                      "algorithmic_pairs_per_launch": node_evals_launch // 2,
                      "executed_fraction": st64.pairs_evaluated / max(1, node_evals_launch // 2),
+                     "executed_tflops": 2 * FLOP_PER_NODE_EVAL * st64.pairs_evaluated / avg_launch_s / 1e12,
+                     "executed_frac": 2 * FLOP_PER_NODE_EVAL * st64.pairs_evaluated / avg_launch_s / 1e12 / peak64,
                      "note": "compressed angular rules evaluate executed_fraction of the "
                              "algorithmic pairs for the same sums (to rounding), so the "
-                             "algorithmic rate exceeds the FP64 pipe peak; the FP64 pipe is "
-                             "~89% busy (profiles/eval_kernel_fp64_production_bubble.md)"},
+                             "algorithmic rate exceeds the FP64 pipe peak; executed_frac counts "
+                             "the same 22 flop per pair actually evaluated; ncu shows the FP64 "
+                             "pipe 89.6% busy (profiles/eval_kernel_fp64_production_bubble.md)"},
         "mixed": {"value": mixed_value, "unit": "points/s", "ms_per_step": 1e3 * tmx / args.steps,
                   "max_rel_err": float(err.max()), "p99_rel_err": float(np.percentile(err, 99)),
                   "median_rel_err": float(np.median(err)), "max_abs_err": float(abs_err.max()),
