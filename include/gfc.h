@@ -146,9 +146,13 @@ int gfc_eval_points(const gfc_propagator *prop, const gfc_params *params,
                     const double *x, int64_t npts, double *G, void *stream);
 
 /* As gfc_eval_points, and if `cond` is not NULL it receives, per point, the
- * scale K_D sum_k M_k of the magnitudes of the node contributions (DEVICE
- * array of npts doubles): the rounding error of a point is a small multiple
- * of the unit roundoff of its precision times this number. */
+ * rounding-error scale K_D (sqrt(sum_k (M_k kappa_k)^2) + sum_k M_k) (DEVICE
+ * array of npts doubles), where M_k is the magnitude of node k's contribution
+ * and kappa_k its relative condition number: |y|/|y + M2| per propagator
+ * factor, (|x| + |y|)/|a| for the angular denominator and, in binary32
+ * (GFC_MIXED), |w|/min_j |1 - w t_j| for the angular sum. The rounding error
+ * of a point is a small multiple of the unit roundoff of its precision times
+ * this number. GFC_F32X2 writes 0 (no scale is computed there). */
 int gfc_eval_points_cond(const gfc_propagator *prop, const gfc_params *params,
                          const double *x, int64_t npts, double *G, double *cond, void *stream);
 

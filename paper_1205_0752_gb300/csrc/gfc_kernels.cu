@@ -37,11 +37,12 @@ g0mu_kernel(const __grid_constant__ KParams kp,
     const PassPre<double, 1> pp1 = pass_pre<double, 1>(kp, P, 0, x);
     for (int k = warp * 32 + lane; k < nn; k += nwarps * 32) {
         Node<double> nd = ray_node<double>(kp, k, P.eth, eD, 0.0);
-        double mag, qm;
+        ErrAcc<double> ea = {0.0, 0.0};
+        double qm;
         int np;
         C<double> v = P.nterm[0] == 2
-                          ? node_value<double, NP, 2>(kp, tab, stab, srules, pp2, x, nd, mag, qm, np)
-                          : node_value<double, NP, 1>(kp, tab, stab, srules, pp1, x, nd, mag, qm, np);
+                          ? node_value<double, NP, 2>(kp, tab, stab, srules, pp2, x, nd, ea, qm, np)
+                          : node_value<double, NP, 1>(kp, tab, stab, srules, pp1, x, nd, ea, qm, np);
         sr += v.r;
         si += v.i;
     }

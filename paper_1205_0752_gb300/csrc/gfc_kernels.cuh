@@ -569,30 +569,55 @@ __device__ __forceinline__ PassPre<T, NT> pass_pre(const KParams &kp, const Plan
     return pp;
 }
 
+// Rounding-error scale of a point's binary32 sum, accumulated per lane: s1 =
+// sum_k M_k, s2 = sum_k (M_k kappa_k)^2, with M_k = |v_k|_1 the magnitude of
+// node k's contribution and kappa_k its relative condition number (below).
+// Rounding errors of different nodes are independent, so they add like a
+// root-sum-square (s2); s1 covers what all nodes share (the rounded per-point
+// and rule constants).
+template <typename T>
+struct ErrAcc {
+    T s1, s2;
+};
+
+__device__ __forceinline__ float trsqrt(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double trsqrt(double x) { return rsqrt(x); }
+__device__ __forceinline__ df trsqrt(df x) { return df(rsqrtf(x.hi), 0.0f); }
+
 // Contribution of one node of one pass: Jt * sum_t c_t P1_t(y)/(y + M2_t) *
 // 2x/a_t * S_t, with the (1 + |y|)^2 scale moved from Jt onto the fractions.
-// `mag` receives the node's error scale (binary32 and cond output only) and
-// `qmin` the smallest |1 - w t|^2 of its angular sums (binary32).
+// The node's error scale is added to `ea` (binary32, and binary64 with cond
+// output); `qmin` receives the smallest |1 - w t|^2 of its angular sums
+// (binary32).
+//
+// kappa_k, the relative sensitivity of the node's value to rounding of its
+// inputs: |y|/|y + M2| per propagator factor (the contour passes near a pole
+// when arg x is near pi), (|x| + |y|)/|a| for the denominator a, and
+// |w|/|1 - w t|_min for the angular sum next to a pinch (binary32 only).
 template <typename T, int NP, int NT>
 __device__ __forceinline__ C<T> node_value(const KParams &kp, const AngTab<T, tab_size<NP>()> &tab,
                                            const T *stab, const void *srules,
                                            const PassPre<T, NT> &pp, C<T> x, const Node<T> &nd,
-                                           T &mag, T &qmin, int &npairs)
+                                           ErrAcc<T> &ea, T &qmin, int &npairs)
 {
+    // double-float has no error-scale output (it would cost registers)
+    const bool want_mag = std::is_same<T, float>::value ||
+                          (std::is_same<T, double>::value && kp.cond_out != nullptr);
     C<T> ia[NT], v[NT], w[NT];
+    T kap[NT];
 #pragma unroll
     for (int s = 0; s < NT; ++s) {
         C<T> a = x + nd.y + pp.m2q[s];
         ia[s] = cinv(a);
         v[s] = T(4) * (nd.y * ia[s]);
         w[s] = (x * v[s]) * ia[s];
+        if (want_mag) kap[s] = (cabs1(x) + cabs1(nd.y)) * rcp(cabs1(a));
     }
     T A[NT], B[NT];
     npairs = pair_sums<T, NP, NT>(kp, tab, kp.npair, stab, srules, w, A, B, qmin) * pp.nt;
     const T Om1 = T(kp.Omega1), del = T(kp.delta);
-    const bool want_mag = sizeof(T) == 4 || kp.cond_out != nullptr;
     C<T> sum = {T(0), T(0)};
-    mag = T(0);
+    T mag = T(0), magk = T(0);
 #pragma unroll
     for (int s = 0; s < NT; ++s) {
         if (s >= pp.nt) break;
@@ -613,15 +638,33 @@ __device__ __forceinline__ C<T> node_value(const KParams &kp, const AngTab<T, ta
             p1 = nd.sc * cinv(nd.y + pp.m2k[s]);
         }
         C<T> f = (pp.cx2[s] * (p1 * pq)) * ia[s];
-        sum = sum + f * S;
+        C<T> fS = f * S;
+        sum = sum + fS;
         if (want_mag) {
-            // rounding scale of S: its parts without cancellation; A and B are
-            // positive sums that carry the sensitivity to w and to each q
-            T Sabs = cabs1(lead) + cabs1(vw) * (A[s] + cabs1(w[s]) * B[s]);
-            mag += cabs1(f) * Sabs;
+            const T ay = cabs1(nd.y);
+            T kq = ay * rcp(cabs1(nd.y + pp.m2q[s]));
+            T kk;
+            if (pp.same[s]) {
+                kk = kq;
+            } else if (pp.full[s]) {
+                C<T> yp = cvt<T>(kp.pc.yp_re, kp.pc.yp_im);
+                kk = ay * (rcp(cabs1(nd.y - yp)) + rcp(cabs1(nd.y - conj(yp))));
+            } else {
+                kk = ay * rcp(cabs1(nd.y + pp.m2k[s]));
+            }
+            const T m = cabs1(fS);
+            mag += m;
+            magk += m * (kap[s] + kq + kk);
         }
     }
-    if (want_mag) mag *= cabs1(nd.Jt);
+    if (want_mag) {
+        const T aj = cabs1(nd.Jt);
+        const T kw = sizeof(T) == 4 ? cabs1(w[0]) * trsqrt(qmin) : T(0);
+        mag = aj * mag;
+        magk = aj * magk + mag * (T(1) + kw);
+        ea.s1 += mag;
+        ea.s2 += magk * magk;
+    }
     return nd.Jt * sum;
 }
 
@@ -691,7 +734,7 @@ template <typename T, int NP, int NTT>
 __device__ __forceinline__ void run_pass(const KParams &kp, const AngTab<T, tab_size<NP>()> &tab,
                                          const T *stab, const void *srules, const Plan<T> &P,
                                          int pass, C<T> x, C<T> eD, int lane, Acc<T> &acc,
-                                         T &amag, T &qall, int &pairs)
+                                         ErrAcc<T> &ea, T &qall, int &pairs)
 {
     const PassPre<T, NTT> pp = pass_pre<T, NTT>(kp, P, pass, x);
     const bool ray = P.kind[pass] == PASS_RAY;
@@ -699,11 +742,10 @@ __device__ __forceinline__ void run_pass(const KParams &kp, const AngTab<T, tab_
     for (int k = lane; k < nn; k += 32) {
         Node<T> nd = ray ? ray_node<T>(kp, k, P.eth, eD, T(0))
                          : detour_node<T>(kp, k, P.eth, eD, P.yp, x);
-        T mag, qm;
+        T qm;
         int np;
-        C<T> v = node_value<T, NP, NTT>(kp, tab, stab, srules, pp, x, nd, mag, qm, np);
+        C<T> v = node_value<T, NP, NTT>(kp, tab, stab, srules, pp, x, nd, ea, qm, np);
         acc_add(acc, v);
-        amag += mag;
         qall = fmin(qall, qm);
         pairs += np;
     }
@@ -714,7 +756,8 @@ __device__ __forceinline__ void run_pass(const KParams &kp, const AngTab<T, tab_
 template <typename T, int NP, int NT>
 __device__ __forceinline__ int point_sum(const KParams &kp, const AngTab<T, tab_size<NP>()> &tab,
                                          const T *stab, const void *srules, double xr, double xi,
-                                         int lane, Acc<T> &acc, T &amag, T &qall, int &pairs)
+                                         int lane, Acc<T> &acc, ErrAcc<T> &ea, T &qall,
+                                         int &pairs)
 {
     const Plan<T> P = make_plan<T>(kp, xr, xi);
     const C<T> x = cvt<T>(xr, xi);
@@ -728,9 +771,9 @@ __device__ __forceinline__ int point_sum(const KParams &kp, const AngTab<T, tab_
         total += P.kind[pass] == PASS_RAY ? kp.n_r : 3 * kp.n_s + kp.n_r;
         if (NT > 1 && P.nterm[pass] == 2)
             run_pass<T, NP, (NT > 1 ? 2 : 1)>(kp, tab, stab, srules, P, pass, x, eD, lane, acc,
-                                             amag, qall, pairs);
+                                             ea, qall, pairs);
         else
-            run_pass<T, NP, 1>(kp, tab, stab, srules, P, pass, x, eD, lane, acc, amag, qall, pairs);
+            run_pass<T, NP, 1>(kp, tab, stab, srules, P, pass, x, eD, lane, acc, ea, qall, pairs);
     }
     return total;
 }
@@ -768,9 +811,10 @@ __device__ __forceinline__ void eval_point(const KParams &kp, const AngTab<T, ta
     }
     Acc<T> acc;
     acc.init();
-    T amag = T(0), qall = T(1e30);
+    ErrAcc<T> ea = {T(0), T(0)};
+    T qall = T(1e30);
     int pairs = 0;
-    int nodes = point_sum<T, NP, NT>(kp, tab, stab, srules, xr, xi, lane, acc, amag, qall, pairs);
+    int nodes = point_sum<T, NP, NT>(kp, tab, stab, srules, xr, xi, lane, acc, ea, qall, pairs);
     if (kp.node_count && lane == 0)
         atomicAdd(kp.node_count, (unsigned long long)nodes * (unsigned long long)(2 * kp.npair));
     if (kp.pair_count) {
@@ -781,7 +825,7 @@ __device__ __forceinline__ void eval_point(const KParams &kp, const AngTab<T, ta
     }
     double sr = warp_sum((double)acc.sr + (double)acc.cr);
     double si = warp_sum((double)acc.si + (double)acc.ci);
-    double cond = kp.K_D * warp_sum((double)amag);
+    double cond = kp.K_D * (sqrt(warp_sum((double)ea.s2)) + warp_sum((double)ea.s1));
     float qpt = (float)qall;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) qpt = fminf(qpt, __shfl_xor_sync(0xffffffffu, qpt, o));
@@ -792,8 +836,8 @@ __device__ __forceinline__ void eval_point(const KParams &kp, const AngTab<T, ta
         if (kp.cond_out) kp.cond_out[p] = cond;
         if (mode == MODE_BULK32 && kp.mixed_rtol > 0.0) {
             // rounding error of the binary32 sum: a small multiple of 2^-24
-            // times the nodes' error scales. Next to a pinch (some node with
-            // |1 - w t| < 3e-3) the discrete sum is so sensitive to the
+            // times the error scale (see ErrAcc). Next to a pinch (some node
+            // with |1 - w t| < 3e-3) the discrete sum is so sensitive to the
             // binary32 rounding of x and of the nodes that no such bound
             // holds; those points go to binary64 too.
             double est = kMixedErrFactor * 5.9604644775390625e-8 * cond;
