@@ -41,7 +41,7 @@ extern "C" {
 #endif
 
 #define GFC_VERSION_MAJOR 1
-#define GFC_VERSION_MINOR 1
+#define GFC_VERSION_MINOR 2
 
 enum {
     GFC_OK = 0,
@@ -83,13 +83,28 @@ typedef enum {
                         pipes; same tolerance target as GFC_FP64               */
 } gfc_precision;
 
+/* Angular rule for int_0^pi f(cos psi) sin^(D-2) psi dpsi (Sect. 4 of the
+ * paper: the angular integral by tanh-sinh quadrature in z = cos psi, with
+ * Gauss-Chebyshev rules of the first and second kind as a check). */
+typedef enum {
+    GFC_ANG_GAUSS_LEGENDRE = 0,  /* Gauss-Legendre in psi on [0, pi] (default) */
+    GFC_ANG_TANH_SINH = 1,       /* tanh-sinh in z with weight (1-z^2)^((D-3)/2):
+                                    z = tanh(pi/2 sinh(k h)), k = -N..N,
+                                    n_angular = 2N + 1 (odd), h = 3/N          */
+    GFC_ANG_CHEBYSHEV1 = 2,      /* psi_j = (j - 1/2) pi/n, weight
+                                    (pi/n) sin^(D-2) psi_j                     */
+    GFC_ANG_CHEBYSHEV2 = 3       /* psi_j = j pi/(n + 1), weight
+                                    pi/(n+1) sin^(D-2) psi_j (Gaussian for D=4) */
+} gfc_angular_rule;
+
 typedef struct {
     int dim;               /* 3 or 4                                           */
     double mu2;            /* subtraction point, real, >= 0; G(mu2) = 0        */
     int n_radial;          /* Gauss-Legendre order on the radial half-line;
                               multiple of 4, 4 <= n_radial <= 16384            */
-    int n_angular;         /* Gauss-Legendre order in psi on [0, pi]; even,
-                              2 <= n_angular <= 512                            */
+    int n_angular;         /* order of the angular rule, 2 <= n_angular <= 512;
+                              odd for tanh-sinh (an odd order puts a node at
+                              psi = pi/2)                                     */
     double radial_scale;   /* L in |q| = L t/(1-t); > 0                        */
     double detour_radius;  /* r of the half circle around a k-leg pole; > 0 and
                               below half the pole's modulus (paper: 0.1)       */
@@ -104,7 +119,10 @@ typedef struct {
                               evaluated again in binary64 (default 1e-6;
                               0 turns this off, leaving the cut band only)     */
     int mixed_fallback;    /* MIXED: arithmetic of the points routed out of
-                              binary32: GFC_FP64 (default) or GFC_F32X2        */
+                              binary32: GFC_F32X2 (default: double-float,
+                              ~48 bits, 2-3x the GB300's FP64 rate) or
+                              GFC_FP64                                          */
+    int angular_rule;      /* gfc_angular_rule (default Gauss-Legendre)        */
 } gfc_params;
 
 /* Cell-centred grid of Kernel 1 (Sect. 4): x_ij = re0 + (i + 1/2)(re1-re0)/m
@@ -135,7 +153,8 @@ const char *gfc_last_error(void);
 int gfc_version(int *major, int *minor);
 
 /* Defaults: D = 4, mu2 = 1, 2048 x 256 nodes, L = 1, r = 0.1, FP64,
- * cut_band 0.05, pinch_angle 0, mixed_rtol 1e-6, mixed_fallback FP64. */
+ * cut_band 0.05, pinch_angle 0, mixed_rtol 1e-6, mixed_fallback F32X2,
+ * angular_rule Gauss-Legendre. */
 int gfc_params_default(gfc_params *p);
 
 /* Steps 4-5 on caller-given points: x and G are DEVICE arrays of npts
@@ -179,8 +198,9 @@ int gfc_eval_points_host(const gfc_propagator *prop, const gfc_params *params,
  * Its node tables and scratch live in one file-scope device array of about
  * 150 KB, so the call allocates nothing (no cudaMalloc, cudaFree or
  * allocating library call); x and G are the caller's DEVICE arrays as for
- * gfc_eval_points. Limits: precision GFC_FP64, n_radial <= 4096,
- * n_angular <= 512; larger sizes or GFC_MIXED give GFC_EINVAL. The array is
+ * gfc_eval_points. Limits: precision GFC_FP64, n_radial <= 4096, even
+ * n_angular <= 512, the Gauss-Legendre angular rule; anything else gives
+ * GFC_EINVAL. The array is
  * shared by every call on a device and keeps the last call's contents: calls
  * that overlap on the GPU (other streams or host threads) race on it. The
  * first call on a device looks up the array's address with that device

@@ -35,7 +35,11 @@ class _Prop(ctypes.Structure):
 class _Params(ctypes.Structure):
     _fields_ = [("dim", ctypes.c_int), ("mu2", ctypes.c_double),
                 ("n_radial", ctypes.c_int), ("n_angular", ctypes.c_int),
-                ("radial_scale", ctypes.c_double), ("detour_radius", ctypes.c_double)]
+                ("radial_scale", ctypes.c_double), ("detour_radius", ctypes.c_double),
+                ("angular_rule", ctypes.c_int)]
+
+# angular rules (Sect. 4)
+ANGULAR_RULES = {"gl": 0, "tanh-sinh": 1, "chebyshev1": 2, "chebyshev2": 3}
 
 
 def _compile(out: str, defines=()) -> None:
@@ -64,6 +68,8 @@ def _bind(path: str):
                                                             ctypes.c_void_p]
     lib.orc_grid_points.restype = ctypes.c_int
     lib.orc_gauss_legendre.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
+    lib.orc_angular_rule.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                                     ctypes.c_void_p]
     lib.orc_gauss_legendre.restype = ctypes.c_int
     return lib
 
@@ -120,6 +126,8 @@ def _params(par: dict) -> _Params:
     q.n_angular = int(par["n_angular"])
     q.radial_scale = float(par.get("radial_scale", 1.0))
     q.detour_radius = float(par.get("detour_radius", 0.1))
+    r = par.get("angular_rule", 0)
+    q.angular_rule = ANGULAR_RULES[r] if isinstance(r, str) else int(r)
     return q
 
 
@@ -156,6 +164,18 @@ def _grid_points(lib, re0, re1, im0, im1, m, n):
     if st != 0:
         raise ValueError("bad grid")
     return x
+
+
+def angular_rule(rule, n: int, dim: int):
+    """Nodes z_j = cos psi_j and weights of an angular rule (Sect. 4) for
+    int_0^pi f(cos psi) sin^(D-2) psi dpsi."""
+    lib = _load()
+    z = np.empty(n)
+    w = np.empty(n)
+    r = ANGULAR_RULES[rule] if isinstance(rule, str) else int(rule)
+    if lib.orc_angular_rule(r, n, dim, z.ctypes.data, w.ctypes.data) != 0:
+        raise ValueError("bad angular rule, order or dimension")
+    return z, w
 
 
 def gauss_legendre(n: int):

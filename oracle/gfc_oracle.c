@@ -379,13 +379,77 @@ static int G0_point(const orc_prop *P, const rules *R, cplx x, cplx *G0, double 
 }
 
 /* ---------------------------------------------------------------------------
+ * Angular rules (Sect. 4: the angular integral by tanh-sinh quadrature in
+ * z = cos psi, Gauss-Chebyshev rules of both kinds as a check). All four
+ * integrate int_0^pi f(cos psi) sin^(D-2) psi dpsi, i.e. int_-1^1 f(z)
+ * (1 - z^2)^((D-3)/2) dz, and return z_j = cos psi_j with weights w_j.
+ *  - GL: Gauss-Legendre in psi on [0, pi], w = (pi/2) w_GL sin^(D-2) psi.
+ *  - tanh-sinh: z = tanh(pi/2 sinh s), s = k h, k = -N..N (n = 2N + 1),
+ *    dz = (pi/2) cosh s / cosh^2(pi/2 sinh s) ds, trapezoid in s; the step
+ *    h = 3/N spans s in [-3, 3] (the paper gives the order only), where
+ *    1 - |z| ~ 1e-14. (1 - z^2)^(1/2) = 1/cosh(pi/2 sinh s) exactly.
+ *  - Chebyshev 1st kind: int g(z)/sqrt(1-z^2) dz ~ (pi/n) sum g(cos psi_j),
+ *    psi_j = (j - 1/2) pi/n, so w_j = (pi/n) sin^(D-2) psi_j.
+ *  - Chebyshev 2nd kind: int g(z) sqrt(1-z^2) dz ~ pi/(n+1) sum sin^2 psi_j
+ *    g(cos psi_j), psi_j = j pi/(n+1), so w_j = pi/(n+1) sin^(D-2) psi_j.
+ * ------------------------------------------------------------------------- */
+int orc_angular_rule(int rule, int n, int dim, double *z, double *w)
+{
+    if (n < 2 || (dim != 3 && dim != 4)) return ORC_EINVAL;
+    if (rule == ORC_ANG_GL) {
+        double *gx = malloc(sizeof(double) * n), *gw = malloc(sizeof(double) * n);
+        if (!gx || !gw) { free(gx); free(gw); return ORC_ENOMEM; }
+        orc_gauss_legendre(n, gx, gw);
+        for (int j = 0; j < n; ++j) {
+            double psi = 0.5 * M_PI * (gx[j] + 1.0), sn = sin(psi);
+            z[j] = cos(psi);
+            w[j] = 0.5 * M_PI * gw[j] * (dim == 4 ? sn * sn : sn);
+            if (ORC_MUTANT == 6) w[j] *= sn;
+        }
+        free(gx);
+        free(gw);
+        return ORC_OK;
+    }
+    if (rule == ORC_ANG_TANH_SINH) {
+        if (n % 2 == 0 || n < 3) return ORC_EINVAL;
+        int N = (n - 1) / 2;
+        double h = 3.0 / N;
+        for (int k = -N; k <= N; ++k) {
+            double s = k * h, u = 0.5 * M_PI * sinh(s), cu = cosh(u);
+            double dz = h * 0.5 * M_PI * cosh(s) / (cu * cu);
+            z[k + N] = tanh(u);
+            w[k + N] = dim == 4 ? dz / cu : dz;
+        }
+        return ORC_OK;
+    }
+    if (rule == ORC_ANG_CHEB1 || rule == ORC_ANG_CHEB2) {
+        for (int j = 1; j <= n; ++j) {
+            double psi = rule == ORC_ANG_CHEB1 ? (j - 0.5) * M_PI / n : j * M_PI / (n + 1);
+            double sn = sin(psi), c = rule == ORC_ANG_CHEB1 ? M_PI / n : M_PI / (n + 1);
+            z[j - 1] = cos(psi);
+            w[j - 1] = c * (dim == 4 ? sn * sn : sn);
+        }
+        return ORC_OK;
+    }
+    return ORC_EINVAL;
+}
+
+/* ---------------------------------------------------------------------------
  * Rules setup / teardown.
  * ------------------------------------------------------------------------- */
+static void rules_free(rules *R)
+{
+    free(R->gr_x); free(R->gr_w); free(R->gs_x); free(R->gs_w);
+    free(R->psi); free(R->wpsi); free(R->cpsi);
+}
+
 static int rules_init(rules *R, const orc_params *Q)
 {
     memset(R, 0, sizeof *R);
     if (Q->dim != 3 && Q->dim != 4) return ORC_EINVAL;
-    if (Q->n_angular < 2 || Q->n_angular % 2) return ORC_EINVAL;
+    if (Q->n_angular < 2) return ORC_EINVAL;
+    if (Q->angular_rule == ORC_ANG_TANH_SINH && Q->n_angular % 2 == 0) return ORC_EINVAL;
+    if (Q->angular_rule < ORC_ANG_GL || Q->angular_rule > ORC_ANG_CHEB2) return ORC_EINVAL;
     if (Q->n_radial < 4 || Q->n_radial % 4) return ORC_EINVAL;
     if (!(Q->radial_scale > 0.0) || !(Q->detour_radius > 0.0)) return ORC_EINVAL;
     R->dim = Q->dim;
@@ -403,29 +467,18 @@ static int rules_init(rules *R, const orc_params *Q)
     R->cpsi = malloc(sizeof(double) * R->n_a);
     orc_gauss_legendre(R->n_r, R->gr_x, R->gr_w);
     orc_gauss_legendre(ns, R->gs_x, R->gs_w);
-    double *gx = malloc(sizeof(double) * R->n_a), *gw = malloc(sizeof(double) * R->n_a);
-    orc_gauss_legendre(R->n_a, gx, gw);
-    for (int j = 0; j < R->n_a; ++j) {
-        double psi = 0.5 * M_PI * (gx[j] + 1.0);
-        double sn = sin(psi);
-        R->psi[j] = psi;
-        R->cpsi[j] = cos(psi);
-        R->wpsi[j] = 0.5 * M_PI * gw[j] * (R->dim == 4 ? sn * sn : sn);
-        if (ORC_MUTANT == 6) R->wpsi[j] *= sn;
+    int rc = orc_angular_rule(Q->angular_rule, R->n_a, R->dim, R->cpsi, R->wpsi);
+    if (rc != ORC_OK) {
+        rules_free(R);
+        return rc;
     }
-    free(gx);
-    free(gw);
+    for (int j = 0; j < R->n_a; ++j) R->psi[j] = acos(R->cpsi[j]);
     /* K_D = S_(D-2) / (2 pi)^D: K_4 = 4 pi/(2 pi)^4, K_3 = 2 pi/(2 pi)^3 (eq. 11) */
     R->K_D = R->dim == 4 ? 4.0 * M_PI / pow(2.0 * M_PI, 4) : 2.0 * M_PI / pow(2.0 * M_PI, 3);
     if (ORC_MUTANT == 4 && R->dim == 4) R->K_D *= 2.0;
     return ORC_OK;
 }
 
-static void rules_free(rules *R)
-{
-    free(R->gr_x); free(R->gr_w); free(R->gs_x); free(R->gs_w);
-    free(R->psi); free(R->wpsi); free(R->cpsi);
-}
 
 static int nodes_alloc(nodes *N, int n_r)
 {

@@ -11,6 +11,9 @@ extern "C" {
 
 enum { ORC_OK = 0, ORC_EINVAL = -1, ORC_ENOMEM = -2 };
 enum { ORC_PROP_SCALAR = 0, ORC_PROP_CPAIR = 1, ORC_PROP_DRESSED = 2 };
+/* angular rules (Sect. 4): Gauss-Legendre in psi (default), tanh-sinh in
+ * z = cos psi (the paper's), Gauss-Chebyshev of the first and second kind */
+enum { ORC_ANG_GL = 0, ORC_ANG_TANH_SINH = 1, ORC_ANG_CHEB1 = 2, ORC_ANG_CHEB2 = 3 };
 
 typedef struct {
     int kind;
@@ -23,12 +26,17 @@ typedef struct {
 typedef struct {
     int dim;                    /* 3 or 4                                     */
     double mu2;                 /* subtraction point, real >= 0               */
-    int n_radial, n_angular;    /* GL orders; n_radial % 4 == 0, n_angular even */
+    int n_radial, n_angular;    /* orders; n_radial % 4 == 0; n_angular >= 2,
+                                   odd for tanh-sinh                          */
     double radial_scale;        /* L in |q| = L t/(1-t)                       */
     double detour_radius;       /* r of the half circle around a swept pole   */
+    int angular_rule;           /* ORC_ANG_*                                  */
 } orc_params;
 
 int orc_gauss_legendre(int n, double *x, double *w);
+/* n nodes z_j = cos psi_j and weights w_j of the angular rule for
+ * int_0^pi f(cos psi) sin^(D-2) psi dpsi = int_-1^1 f(z) (1-z^2)^((D-3)/2) dz */
+int orc_angular_rule(int rule, int n, int dim, double *z, double *w);
 /* x, G interleaved complex128 (re, im); kappa optional (may be NULL). */
 int orc_eval_points(const orc_prop *P, const orc_params *Q, const double *x, long npts,
                     double *G, double *kappa, int nthreads);

@@ -96,7 +96,7 @@ void gauss_legendre(int n, std::vector<double> &x, std::vector<double> &w)
 // node tables (per device, cached by rule)
 // ---------------------------------------------------------------------------
 struct Tables {
-    int n_r, n_a, dim;
+    int n_r, n_a, dim, ang_rule;
     double L;
     double2 *rad64 = nullptr, *seg64 = nullptr, *arc64 = nullptr;
     float2 *rad32 = nullptr, *seg32 = nullptr, *arc32 = nullptr;
@@ -291,7 +291,7 @@ static thread_local LastCall g_last_call;
 constexpr int kMaxG0Warps = 512;
 
 struct DeviceState {
-    std::map<std::tuple<int, int, int, double>, std::unique_ptr<Tables>> tables;
+    std::map<std::tuple<int, int, int, double, int>, std::unique_ptr<Tables>> tables;
     std::map<cudaStream_t, std::unique_ptr<Scratch>> scratch;
 };
 
@@ -332,6 +332,45 @@ static int upload(V **dst, const std::vector<V> &src, size_t &bytes)
     return GFC_OK;
 }
 
+// Nodes z_j = cos psi_j (descending in z) and weights w_j of the angular rule
+// for int_0^pi f(cos psi) sin^(D-2) psi dpsi (Sect. 4: tanh-sinh in z, with
+// Gauss-Chebyshev rules of both kinds as a check; Gauss-Legendre in psi by
+// default). Every rule is symmetric: z_(n-1-j) = -z_j.
+static void angular_nodes(int rule, int n, int dim, std::vector<double> &z, std::vector<double> &w)
+{
+    const double pi = 3.14159265358979323846;
+    auto sinpow = [dim](double s) { return dim == 4 ? s * s : s; };
+    if (rule == GFC_ANG_TANH_SINH) {
+        // trapezoid in s = k h on [-3, 3] for z = tanh(pi/2 sinh s); the
+        // factor (1 - z^2)^(1/2) of D = 4 is 1/cosh(pi/2 sinh s) exactly
+        const int N = (n - 1) / 2;
+        const double h = 3.0 / N;
+        for (int i = 0; i < n; ++i) {
+            const double s = (N - i) * h, u = 0.5 * pi * std::sinh(s), cu = std::cosh(u);
+            const double dz = h * 0.5 * pi * std::cosh(s) / (cu * cu);
+            z[i] = std::tanh(u);
+            w[i] = dim == 4 ? dz / cu : dz;
+        }
+        return;
+    }
+    if (rule == GFC_ANG_CHEBYSHEV1 || rule == GFC_ANG_CHEBYSHEV2) {
+        const bool first = rule == GFC_ANG_CHEBYSHEV1;
+        for (int i = 0; i < n; ++i) {
+            const double psi = first ? (i + 0.5) * pi / n : (i + 1) * pi / (n + 1);
+            z[i] = std::cos(psi);
+            w[i] = (first ? pi / n : pi / (n + 1)) * sinpow(std::sin(psi));
+        }
+        return;
+    }
+    std::vector<double> gx, gw;
+    gauss_legendre(n, gx, gw);
+    for (int i = 0; i < n; ++i) {
+        const double psi = 0.5 * pi * (gx[i] + 1.0);
+        z[i] = std::cos(psi);
+        w[i] = 0.5 * pi * gw[i] * sinpow(std::sin(psi));
+    }
+}
+
 static int build_tables(Tables &T)
 {
     const double pi = 3.14159265358979323846;
@@ -359,9 +398,11 @@ static int build_tables(Tables &T)
         arc64[k] = make_double2(std::cos(pi * t), std::sin(pi * t));
         arc32[k] = make_float2((float)std::cos(pi * t), (float)std::sin(pi * t));
     }
-    // angular pairs: psi_j and pi - psi_j on [0, pi], weight w sin^(D-2) psi
-    gauss_legendre(T.n_a, gx, gw);
-    int np = T.n_a / 2;
+    // angular pairs: psi_j and pi - psi_j on [0, pi], weight w sin^(D-2) psi;
+    // an odd rule's centre node psi = pi/2 pairs with itself at half weight
+    std::vector<double> az(T.n_a), aw(T.n_a);
+    angular_nodes(T.ang_rule, T.n_a, T.dim, az, aw);
+    int np = (T.n_a + 1) / 2;
     T.t.resize(np);
     T.e.resize(np);
     T.g.resize(np);
@@ -369,10 +410,9 @@ static int build_tables(Tables &T)
     std::vector<float> ang32(3 * np);
     double Om = 0, Om1 = 0, c_om = 0, c_om1 = 0;
     for (int j = 0; j < np; ++j) {
-        double psi = 0.5 * pi * (gx[j] + 1.0);
-        double sn = std::sin(psi), cs = std::cos(psi);
-        double w = 0.5 * pi * gw[j] * (T.dim == 4 ? sn * sn : sn);
-        double t = cs * cs;
+        const bool centre = 2 * j + 1 == T.n_a;
+        double w = centre ? 0.5 * aw[j] : aw[j];
+        double t = centre ? 0.0 : az[j] * az[j];
         T.t[j] = t;
         T.e[j] = w * t * t;
         T.g[j] = w * t * t * t;
@@ -432,11 +472,11 @@ static int get_device(int *dev)
     return GFC_OK;
 }
 
-int get_tables(int dev, int n_r, int n_a, int dim, double L, Tables **out)
+int get_tables(int dev, int n_r, int n_a, int dim, double L, int ang_rule, Tables **out)
 {
     std::lock_guard<std::mutex> lk(g_mu);
     auto &ds = g_dev[dev];
-    auto key = std::make_tuple(n_r, n_a, dim, L);
+    auto key = std::make_tuple(n_r, n_a, dim, L, ang_rule);
     auto it = ds.tables.find(key);
     if (it != ds.tables.end()) {
         *out = it->second.get();
@@ -447,6 +487,7 @@ int get_tables(int dev, int n_r, int n_a, int dim, double L, Tables **out)
     T->n_a = n_a;
     T->dim = dim;
     T->L = L;
+    T->ang_rule = ang_rule;
     int st = build_tables(*T);
     if (st != GFC_OK) {
         free_tables(*T);
@@ -495,8 +536,12 @@ static int check_params(const gfc_params *p)
     if (!(p->mu2 >= 0.0) || !std::isfinite(p->mu2)) return fail(GFC_EINVAL, "mu2 must be >= 0");
     if (p->n_radial < 4 || p->n_radial > kMaxRadial || p->n_radial % 4)
         return fail(GFC_EINVAL, "n_radial must be a multiple of 4 in [4, 16384]");
-    if (p->n_angular < 2 || p->n_angular > kMaxAngular || p->n_angular % 2)
-        return fail(GFC_EINVAL, "n_angular must be even in [2, 512]");
+    if (p->n_angular < 2 || p->n_angular > kMaxAngular)
+        return fail(GFC_EINVAL, "n_angular must be in [2, 512]");
+    if (p->angular_rule < GFC_ANG_GAUSS_LEGENDRE || p->angular_rule > GFC_ANG_CHEBYSHEV2)
+        return fail(GFC_EINVAL, "angular_rule must be a gfc_angular_rule");
+    if (p->angular_rule == GFC_ANG_TANH_SINH && (p->n_angular % 2 == 0 || p->n_angular < 3))
+        return fail(GFC_EINVAL, "the tanh-sinh rule needs an odd n_angular >= 3");
     if (!(p->radial_scale > 0.0) || !std::isfinite(p->radial_scale))
         return fail(GFC_EINVAL, "radial_scale must be > 0");
     if (!(p->detour_radius > 0.0)) return fail(GFC_EINVAL, "detour_radius must be > 0");
@@ -569,7 +614,7 @@ static void fill_kparams_tables(KParams &kp, const gfc_params *p, const Tables &
     kp.dim = p->dim;
     kp.n_r = p->n_radial;
     kp.n_s = p->n_radial / 4;
-    kp.npair = p->n_angular / 2;
+    kp.npair = (p->n_angular + 1) / 2;
     kp.rad64 = T.rad64;
     kp.rad32 = T.rad32;
     kp.seg64 = T.seg64;
@@ -651,7 +696,9 @@ static int run(const gfc_propagator *prop, const gfc_params *p, KParams kp_point
     int dev;
     if ((rc = get_device(&dev))) return rc;
     Tables *T;
-    if ((rc = get_tables(dev, p->n_radial, p->n_angular, p->dim, p->radial_scale, &T))) return rc;
+    if ((rc = get_tables(dev, p->n_radial, p->n_angular, p->dim, p->radial_scale, p->angular_rule,
+                         &T)))
+        return rc;
     Scratch *S;
     if ((rc = get_scratch(dev, st, &S))) return rc;
     if (p->precision == GFC_MIXED && (rc = grow_list(*S, kp_points.npts))) return rc;
@@ -714,9 +761,10 @@ int make_prop_c(const void *prop, const void *params, PropConst &pc)
     return make_prop((const gfc_propagator *)prop, (const gfc_params *)params, pc);
 }
 
-int get_tables_c(int dev, int n_r, int n_a, int dim, double L, Tables **out, size_t *bytes)
+int get_tables_c(int dev, int n_r, int n_a, int dim, double L, int ang_rule, Tables **out,
+                 size_t *bytes)
 {
-    int rc = get_tables(dev, n_r, n_a, dim, L, out);
+    int rc = get_tables(dev, n_r, n_a, dim, L, ang_rule, out);
     if (rc == GFC_OK && bytes) *bytes = (*out)->bytes;
     return rc;
 }
@@ -773,7 +821,8 @@ int gfc_params_default(gfc_params *p)
     p->cut_band = 0.05;
     p->pinch_angle = 0.0;
     p->mixed_rtol = 1e-6;
-    p->mixed_fallback = GFC_FP64;
+    p->mixed_fallback = GFC_F32X2;
+    p->angular_rule = GFC_ANG_GAUSS_LEGENDRE;
     return GFC_OK;
 }
 

@@ -154,7 +154,8 @@ int cuda_fail(cudaError_t e, const char *what);
 int check_params_c(const void *params);
 int check_grid_c(const void *grid);
 int make_prop_c(const void *prop, const void *params, PropConst &pc);
-int get_tables_c(int dev, int n_r, int n_a, int dim, double L, Tables **out, size_t *bytes);
+int get_tables_c(int dev, int n_r, int n_a, int dim, double L, int ang_rule, Tables **out,
+                 size_t *bytes);
 void fill_kparams_c(KParams &kp, const void *params, const Tables &T, const PropConst &pc);
 DevTables dev_tables_c(const Tables &T);
 

@@ -400,6 +400,11 @@ __device__ __forceinline__ df q_direct(df t, df wr, df wi)
     df di = wi * t;
     return fma(dr, dr, di * di);
 }
+// e r + acc for the positive angular sums A and B (double-float: an add that
+// may assume no cancellation)
+__device__ __forceinline__ float fma_pos(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double fma_pos(double a, double b, double c) { return fma(a, b, c); }
+
 template <typename T>
 __device__ __forceinline__ T q_horner(T t, T w2, T m2wr)
 {
@@ -452,6 +457,23 @@ __device__ __forceinline__ void rule_node(const void *srules, int k, float &t, f
     g = v.z;
 }
 
+// Unroll factors of the runtime-length angular pair loops. Double-float
+// bodies are several times larger than binary64 ones; unrolled they no longer
+// fit the instruction cache (measured on GB300, production bubble grid:
+// unroll 4 / 2 / 1 gives 2.95 / 3.74 / 4.06 Mpoints/s in double-float).
+#ifndef GFC_DF_UNROLL
+#define GFC_DF_UNROLL 1
+#endif
+#ifndef GFC_F32_UNROLL
+#define GFC_F32_UNROLL 4
+#endif
+template <typename T>
+__host__ __device__ constexpr int pair_unroll()
+{
+    return std::is_same<T, df>::value ? GFC_DF_UNROLL
+                                      : (std::is_same<T, float>::value ? GFC_F32_UNROLL : 4);
+}
+
 // Angular sums A = sum e_j/q_j, B = sum g_j/q_j for NT terms; qmin (binary32
 // only) is the smallest q met, a measure of how close the node is to a pinch.
 template <typename T, int NP, int NT>
@@ -484,7 +506,7 @@ __device__ __forceinline__ int pair_sums(const KParams &kp, const AngTab<T, tab_
     }
     if (rule < kp.nrule) {
         const int off = kp.rule_off[rule], n = kp.rule_n[rule];
-#pragma unroll 4
+#pragma unroll (pair_unroll<T>())
         for (int k = 0; k < n; ++k) {
             T t, e, g;
             rule_node(srules, off + k, t, e, g);
@@ -493,8 +515,8 @@ __device__ __forceinline__ int pair_sums(const KParams &kp, const AngTab<T, tab_
                 T q = f32 ? q_direct(t, w[s].r, w[s].i) : q_horner(t, w2[s], m2wr[s]);
                 if (f32) qm = fmin(qm, q);
                 T r = rcp(q);
-                A[s] = fma(e, r, A[s]);
-                B[s] = fma(g, r, B[s]);
+                A[s] = fma_pos(e, r, A[s]);
+                B[s] = fma_pos(g, r, B[s]);
             }
         }
     } else if (NP > 0) {
@@ -507,16 +529,16 @@ __device__ __forceinline__ int pair_sums(const KParams &kp, const AngTab<T, tab_
                 if (f32) qm = fmin(qm, q);
                 T r = rcp(q);
                 if (j & 1) {
-                    A1[s] = fma(e, r, A1[s]);
-                    B1[s] = fma(g, r, B1[s]);
+                    A1[s] = fma_pos(e, r, A1[s]);
+                    B1[s] = fma_pos(g, r, B1[s]);
                 } else {
-                    A[s] = fma(e, r, A[s]);
-                    B[s] = fma(g, r, B[s]);
+                    A[s] = fma_pos(e, r, A[s]);
+                    B[s] = fma_pos(g, r, B[s]);
                 }
             }
         }
     } else {
-#pragma unroll 4
+#pragma unroll (pair_unroll<T>())
         for (int j = 0; j < npair; ++j) {
             const T t = stab[3 * j], e = stab[3 * j + 1], g = stab[3 * j + 2];
 #pragma unroll
@@ -524,8 +546,8 @@ __device__ __forceinline__ int pair_sums(const KParams &kp, const AngTab<T, tab_
                 T q = q_direct(t, w[s].r, w[s].i);
                 if (f32) qm = fmin(qm, q);
                 T r = rcp(q);
-                A[s] = fma(e, r, A[s]);
-                B[s] = fma(g, r, B[s]);
+                A[s] = fma_pos(e, r, A[s]);
+                B[s] = fma_pos(g, r, B[s]);
             }
         }
     }

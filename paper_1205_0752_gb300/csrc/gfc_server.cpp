@@ -94,7 +94,9 @@ struct LaunchRec {
     int64_t *offs_host = nullptr;       // pinned
 };
 
-using GroupKey = std::tuple<int, int, int, int, int>;   // arith, npair, dim, two, mode
+// arith, npair, dim, two terms, mode, angular rule: the requests of one launch
+// share its angular tables
+using GroupKey = std::tuple<int, int, int, int, int, int>;
 
 }  // namespace
 
@@ -172,7 +174,7 @@ double work_per_point(const Request &r, int arith)
     double nodes = r.params.n_radial;
     if (r.prop.kind != GFC_PROP_SCALAR) nodes *= 1.75;
     double terms = r.prop.kind == GFC_PROP_DRESSED ? 2.0 : 1.0;
-    double w = nodes * (r.params.n_angular / 2) * terms;
+    double w = nodes * ((r.params.n_angular + 1) / 2) * terms;
     return arith == ARITH_F32 ? w : (arith == ARITH_DF ? w * kDfWeight : w * kFp64Weight);
 }
 
@@ -216,7 +218,7 @@ void finish(gfc_server *s, Request *r, int status)
 int admit(gfc_server *s, Request *r)
 {
     int rc = get_tables_c(s->device, r->params.n_radial, r->params.n_angular, r->params.dim,
-                          r->params.radial_scale, &r->T, nullptr);
+                          r->params.radial_scale, r->params.angular_rule, &r->T, nullptr);
     if (rc) return rc;
     PropConst pc;
     if ((rc = make_prop_c(&r->prop, &r->params, pc))) return rc;
@@ -290,8 +292,8 @@ void issue_launches(gfc_server *s)
         for (int p = 0; p < (int)r->phases.size(); ++p) {
             const Phase &ph = r->phases[p];
             if (ph.end < 0 || ph.next >= ph.end) continue;
-            GroupKey k{ph.arith, r->params.n_angular / 2, r->params.dim,
-                       r->prop.kind == GFC_PROP_DRESSED ? 1 : 0, ph.mode};
+            GroupKey k{ph.arith, (r->params.n_angular + 1) / 2, r->params.dim,
+                       r->prop.kind == GFC_PROP_DRESSED ? 1 : 0, ph.mode, r->params.angular_rule};
             groups[k].push_back({r, p});
         }
     }

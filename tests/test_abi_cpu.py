@@ -30,7 +30,7 @@ def test_every_declared_function_is_exported():
 
 
 def test_version_and_strings():
-    assert gfc.version() == (1, 1)
+    assert gfc.version() == (1, 2)
     lib = gfc.load_library()
     assert lib.gfc_strerror(0) == b"ok"
     assert lib.gfc_strerror(-3) == b"request exceeds the memory budget"
@@ -40,11 +40,14 @@ def test_defaults():
     p = gfc.make_params()
     assert (p.dim, p.mu2, p.n_radial, p.n_angular) == (4, 1.0, 2048, 256)
     assert (p.radial_scale, p.detour_radius, p.precision) == (1.0, 0.1, 0)
-    assert (p.cut_band, p.pinch_angle, p.mixed_rtol, p.mixed_fallback) == (0.05, 0.0, 1e-6, 0)
+    assert (p.cut_band, p.pinch_angle, p.mixed_rtol, p.mixed_fallback) == (0.05, 0.0, 1e-6, 2)
+    assert p.angular_rule == 0
 
 
 @pytest.mark.parametrize("bad", [dict(dim=2), dict(n_radial=6), dict(n_radial=20000),
-                                 dict(n_angular=3), dict(n_angular=1024), dict(mu2=-1.0),
+                                 dict(n_angular=1), dict(n_angular=1024), dict(mu2=-1.0),
+                                 dict(angular_rule="tanh-sinh", n_angular=64),
+                                 dict(angular_rule=4),
                                  dict(radial_scale=-1.0), dict(precision=7),
                                  dict(mixed_rtol=-1.0), dict(mixed_fallback="mixed")])
 def test_bad_params_rejected_on_the_host(bad):

@@ -195,6 +195,50 @@ def test_convergence_under_refinement():
     assert errs[2] < 1e-5 * abs(ref)
 
 
+@pytest.mark.parametrize("dim", [3, 4])
+@pytest.mark.parametrize("rule,n", [("gl", 64), ("tanh-sinh", 49), ("tanh-sinh", 97),
+                                    ("chebyshev1", 64), ("chebyshev2", 64)])
+def test_angular_rule_moments(rule, n, dim):
+    """Sect. 4's angular rules against the moments int_0^pi cos^(2k) psi
+    sin^(D-2) psi dpsi = Gamma(k + 1/2) Gamma((D-1)/2) / Gamma(k + D/2):
+    Gauss rules are exact to their degree, tanh-sinh converges doubly
+    exponentially, the Chebyshev rules are Gaussian for the weight of one
+    dimension only (2nd kind: D = 4) and converge algebraically for D = 3."""
+    from math import gamma
+    z, w = oracle.angular_rule(rule, n, dim)
+    assert np.all(np.abs(z) < 1.0) and np.all(w > 0.0)
+    assert np.max(np.abs(np.sort(z) + np.sort(z)[::-1])) < 1e-15       # symmetric in z
+    exact = np.array([gamma(k + 0.5) * gamma((dim - 1) / 2) / gamma(k + dim / 2) for k in range(12)])
+    got = np.array([np.sum(w * z ** (2 * k)) for k in range(12)])
+    err = np.abs(got - exact) / exact
+    if rule == "gl" or (rule.startswith("chebyshev") and dim == 4):
+        assert err.max() < 1e-13
+    elif rule == "tanh-sinh":
+        assert err[:4].max() < (1e-13 if n > 64 else 1e-11) and err.max() < 1e-8
+    else:
+        z4, w4 = oracle.angular_rule(rule, 4 * n, dim)
+        err4 = abs(np.sum(w4) - exact[0]) / exact[0]
+        assert 1e-6 < err[0] < 1e-2 and err4 < err[0] / 8          # O(n^-2)
+
+
+@pytest.mark.parametrize("rule,n,tol", [("gl", 64, 1e-12), ("tanh-sinh", 97, 1e-11),
+                                        ("chebyshev1", 64, 1e-12), ("chebyshev2", 64, 1e-12)])
+def test_angular_rules_reach_the_closed_form(rule, n, tol):
+    """Every angular rule reproduces the D = 4 bubble's closed form away from
+    the negative real axis; the paper's 49-node tanh-sinh rule is exact there
+    only where the integrand is benign and improves with the order."""
+    prop = {"kind": "scalar", "m2": 1.0}
+    xs = np.array([2 + 1j, -2 + 3j, 0.5 - 2j])
+    ref = np.array([G_exact(prop, x, 4, 1.0) for x in xs])
+    G = oracle.eval_points(prop, dict(dim=4, mu2=1.0, n_radial=1024, n_angular=n,
+                                      angular_rule=rule), xs)
+    assert np.max(np.abs(G - ref) / np.abs(ref)) < tol
+    G49 = oracle.eval_points(prop, dict(dim=4, mu2=1.0, n_radial=1024, n_angular=49,
+                                        angular_rule="tanh-sinh"), xs)
+    e49 = np.abs(G49 - ref) / np.abs(ref)
+    assert e49[0] < 1e-13 and e49[1] > np.max(np.abs(G - ref)[1] / np.abs(ref[1]))
+
+
 def test_condition_number_reported():
     """kappa = sum|terms|/|sum| grows as x approaches the negative real axis,
     where the angular integrand nearly pinches."""
@@ -206,7 +250,8 @@ def test_condition_number_reported():
 
 
 @pytest.mark.parametrize("bad", [
-    dict(dim=5), dict(n_angular=63), dict(n_radial=250), dict(radial_scale=0.0),
+    dict(dim=5), dict(n_angular=1), dict(n_radial=250), dict(radial_scale=0.0),
+    dict(angular_rule="tanh-sinh"), dict(angular_rule=7),
 ])
 def test_rejects_bad_parameters(bad):
     par = dict(dim=4, mu2=1.0, n_radial=256, n_angular=64)

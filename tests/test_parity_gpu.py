@@ -38,7 +38,7 @@ def assert_parity(G, ref, rtol, x=None, what=""):
 
 def oracle_params(p):
     return {k: p[k] for k in ("dim", "mu2", "n_radial", "n_angular", "radial_scale",
-                              "detour_radius") if k in p}
+                              "detour_radius", "angular_rule") if k in p}
 
 
 def run_grid(prop, params, rect, m, n):
@@ -136,7 +136,8 @@ def test_edge_points():
 
 def test_rejects_bad_arguments():
     x = torch.tensor([1 + 1j], dtype=torch.complex128, device="cuda")
-    for bad in (dict(dim=5), dict(n_angular=7), dict(n_radial=6), dict(radial_scale=0.0)):
+    for bad in (dict(dim=5), dict(n_angular=1), dict(angular_rule="tanh-sinh", n_angular=8),
+                dict(n_radial=6), dict(radial_scale=0.0)):
         with pytest.raises(gfc.GfcError):
             gfc.eval_points(SCALAR, dict(bad), x)
     with pytest.raises(gfc.GfcError):
@@ -199,16 +200,46 @@ def test_dressed_full_size_sampled(precision, dim):
         assert_parity(G[idx], ref, RTOL[precision], x, f"dressed 512^2 D={dim} draw {k} {precision}")
 
 
+@pytest.mark.parametrize("fallback", ["f32x2", "fp64"])
 @pytest.mark.parametrize("kind", ["bubble", "paper"])
-def test_mixed_with_double_float_fallback(kind):
-    """Mixed precision whose routed points go to the double-float kernel."""
+def test_mixed_fallback_arithmetics(kind, fallback):
+    """Mixed precision whose routed points go to the double-float kernel (the
+    default) or to the binary64 kernel."""
     if kind == "bubble":
         prop, rect, m, n, mu2 = SCALAR, si.grid_rect("small"), 64, 64, 1.0
     else:
         prop, rect, m, n, mu2 = PAPER, si.grid_rect("paper"), 128, 128, 0.0
     par = dict(dim=4, mu2=mu2, n_radial=256, n_angular=64, precision="mixed",
-               mixed_fallback="f32x2")
+               mixed_fallback=fallback)
     G = run_grid(prop, par, rect, m, n)
     x = oracle.grid_points(*rect, m, n)
     ref = oracle.eval_points(prop, oracle_params(par), x)
-    assert_parity(G, ref, RTOL["mixed"], x, f"mixed/f32x2 {kind}")
+    assert_parity(G, ref, RTOL["mixed"], x, f"mixed/{fallback} {kind}")
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed", "f32x2"])
+@pytest.mark.parametrize("rule,n", [("tanh-sinh", 49), ("tanh-sinh", 65), ("chebyshev1", 64),
+                                    ("chebyshev2", 64), ("chebyshev1", 63), ("gl", 63)])
+def test_angular_rules(rule, n, precision):
+    """The paper's angular rules (Sect. 4: tanh-sinh in z, Gauss-Chebyshev of
+    both kinds) and odd orders, whose centre node pairs with itself; n = 63
+    and 64 run the unrolled 32-pair kernels, 49 and 65 the generic loop."""
+    par = dict(dim=4, mu2=1.0, n_radial=256, n_angular=n, angular_rule=rule, precision=precision)
+    rect = si.grid_rect("small")
+    G = run_grid(SCALAR, par, rect, 48, 40)
+    x = oracle.grid_points(*rect, 48, 40)
+    ref = oracle.eval_points(SCALAR, oracle_params(par), x)
+    assert_parity(G, ref, RTOL[precision], x, f"{rule} n={n} {precision}")
+
+
+@pytest.mark.parametrize("dim", [3, 4])
+def test_paper_rule_on_the_dressed_propagator(dim):
+    """The paper's 49-node tanh-sinh rule with detours and two-term passes."""
+    a, b, c = si.dressed_draws(3, 1)[0]
+    prop = {"kind": "dressed", "a": a, "b": b, "c": c}
+    par = dict(dim=dim, mu2=1.0, n_radial=512, n_angular=49, angular_rule="tanh-sinh")
+    rect = si.grid_rect("small")
+    G = run_grid(prop, par, rect, 32, 24)
+    x = oracle.grid_points(*rect, 32, 24)
+    ref = oracle.eval_points(prop, oracle_params(par), x)
+    assert_parity(G, ref, RTOL["fp64"], x, f"dressed tanh-sinh D={dim}")

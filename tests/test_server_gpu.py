@@ -98,6 +98,6 @@ def test_cancel_queued_and_wait_timeout():
 def test_bad_requests_rejected():
     with gfc.Server(0, hbm_budget_bytes=1 << 30, max_slots=2) as srv:
         with pytest.raises(gfc.GfcError):
-            srv.submit({"kind": "scalar", "m2": 1.0}, dict(n_angular=7), (*RECT, 8, 8))
+            srv.submit({"kind": "scalar", "m2": 1.0}, dict(n_angular=1), (*RECT, 8, 8))
         with pytest.raises(gfc.GfcError):
             srv.submit({"kind": "scalar", "m2": 1.0}, {}, (-2.0, 1.0, -1.5, 1.5, 4, 3))
