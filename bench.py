@@ -337,6 +337,15 @@ def run_gfc(args):
         tts, _ = timed(parts, 1, 1)
         paper_rule[prec] = ws * npts_step / tts
 
+    # ---- the psi integral in closed form (no angular quadrature error) -----
+    exact_rule = {}
+    for nr in (NR, 4 * NR):
+        for prec in ("fp64", "f32x2", "mixed"):
+            parex = gfc.make_params(dim=4, mu2=1.0, n_radial=nr, n_angular=2,
+                                    angular_rule="exact", precision=prec)
+            tex, _ = timed(parex, 1, 1)
+            exact_rule[f"{prec}_nr{nr}"] = ws * npts_step / tex
+
     # ---- end to end through the host-buffer C-ABI call --------------------
     import oracle  # grid points of the block, written by the oracle's Kernel 1
     xh = torch.from_numpy(oracle.grid_points(*rect, side, side)).pin_memory()
@@ -408,6 +417,9 @@ def run_gfc(args):
                                "n_radial": NR, "unit": "points/s",
                                "fp64": paper_rule["fp64"], "f32x2": paper_rule["f32x2"],
                                "mixed": paper_rule["mixed"]},
+        "exact_angular": dict({"rule": "psi integral in closed form (limit of every angular "
+                                         "rule); radial Gauss-Legendre n_radial as named",
+                               "unit": "points/s"}, **exact_rule),
         "e2e": {"value": e2e_value, "unit": "points/s", "h2d_bytes_per_step": 3 * 16 * side * side,
                 "d2h_bytes_per_step": 3 * 16 * side * side},
     }

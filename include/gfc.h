@@ -93,8 +93,13 @@ typedef enum {
                                     n_angular = 2N + 1 (odd), h = 3/N          */
     GFC_ANG_CHEBYSHEV1 = 2,      /* psi_j = (j - 1/2) pi/n, weight
                                     (pi/n) sin^(D-2) psi_j                     */
-    GFC_ANG_CHEBYSHEV2 = 3       /* psi_j = j pi/(n + 1), weight
+    GFC_ANG_CHEBYSHEV2 = 3,      /* psi_j = j pi/(n + 1), weight
                                     pi/(n+1) sin^(D-2) psi_j (Gaussian for D=4) */
+    GFC_ANG_EXACT = 4            /* the angular integral in closed form, the
+                                    limit n -> infinity of every rule above:
+                                    no quadrature error in psi, which dominates
+                                    next to the negative real axis;
+                                    n_angular is ignored                       */
 } gfc_angular_rule;
 
 typedef struct {

@@ -39,7 +39,7 @@ class _Params(ctypes.Structure):
                 ("angular_rule", ctypes.c_int)]
 
 # angular rules (Sect. 4)
-ANGULAR_RULES = {"gl": 0, "tanh-sinh": 1, "chebyshev1": 2, "chebyshev2": 3}
+ANGULAR_RULES = {"gl": 0, "tanh-sinh": 1, "chebyshev1": 2, "chebyshev2": 3, "exact": 4}
 
 
 def _compile(out: str, defines=()) -> None:

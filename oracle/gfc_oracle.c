@@ -162,6 +162,7 @@ typedef struct {
     double *gs_x, *gs_w;     /* GL on [-1,1], n_r/4 nodes (detour segments) */
     double *psi, *wpsi;      /* angular: psi_j, w_j sin^(D-2) psi_j */
     double *cpsi;            /* cos psi_j */
+    int exact;               /* psi integral in closed form */
     double K_D;
 } rules;
 
@@ -261,6 +262,37 @@ static double choose_ray(double phi, const cplx *ypoles, int npoles)
 }
 
 /* ---------------------------------------------------------------------------
+ * The psi integral in closed form. With s = x + y - B cos psi, B = 2 sqrt(x)
+ * sqrt(y), a pole leg 1/(s + M2) has A = x + y + M2 and
+ *   int_0^pi sin^2 psi dpsi/(A - B cos psi) = pi/(A (1 + sqrt(1 - B^2/A^2)))
+ *   int_0^pi sin psi dpsi/(A - B cos psi) = (2/A) artanh(B/A)/(B/A)
+ * (the first by the substitution t = tan(psi/2) and residues, the second by
+ * z = cos psi), principal branches, which continue the real-positive case
+ * analytically off B^2/A^2 in [1, inf). A dressed leg is split into its two
+ * poles: (s + a)/((s - r1)(s - r2)) = R1/(s - r1) + R2/(s - r2).
+ * ------------------------------------------------------------------------- */
+static cplx pole_angular(int dim, cplx A, cplx B2)
+{
+    cplx w = B2 / (A * A);
+    if (dim == 4) return M_PI / (A * (1.0 + csqrt(1.0 - w)));
+    cplx z = csqrt(w);
+    return cabs(z) < 1e-8 ? 2.0 / A * (1.0 + w / 3.0) : 2.0 / A * catanh(z) / z;
+}
+
+/* int_0^pi sin^(D-2) psi [P2(s(psi)) - P2(y)] dpsi for one leg */
+static cplx leg_angular(const leg *L, int dim, cplx x, cplx y)
+{
+    cplx B2 = 4.0 * x * y;
+    double wtot = dim == 4 ? 0.5 * M_PI : 2.0;
+    if (L->form == PL_POLE) return pole_angular(dim, x + y + L->M2, B2) - wtot * leg_eval(L, y);
+    double disc = 4.0 * L->c - L->b * L->b;
+    cplx r1 = 0.5 * (-L->b + I * sqrt(disc)), r2 = conj(r1);
+    cplx R1 = (r1 + L->a) / (r1 - r2), R2 = (r2 + L->a) / (r2 - r1);
+    return R1 * pole_angular(dim, x + y - r1, B2) + R2 * pole_angular(dim, x + y - r2, B2)
+           - wtot * leg_eval(L, y);
+}
+
+/* ---------------------------------------------------------------------------
  * One term: coef * int_C dy 1/2 y^((D-2)/2) int dpsi w(psi) P1(y)[P2(s) - P2(y)]
  * ------------------------------------------------------------------------- */
 static void term_sum(const rules *R, cplx x, cplx coef, const leg *P1, const leg *P2,
@@ -274,7 +306,12 @@ static void term_sum(const rules *R, cplx x, cplx coef, const leg *P1, const leg
         cplx p1 = leg_eval(P1, y);
         nsum inner = {0, 0, 0, 0};
         double ainner = 0.0;
-        for (int j = 0; j < R->n_a; ++j) {
+        if (R->exact) {
+            cplx f = p1 * leg_angular(P2, R->dim, x, y);
+            nsum_add(&inner, f);
+            ainner = cabs(f);
+        }
+        for (int j = 0; j < (R->exact ? 0 : R->n_a); ++j) {
             cplx ymS = (ORC_MUTANT == 5 ? 0.0 : -x) + 2.0 * sx * sy * R->cpsi[j];  /* y - s */
             cplx s = y - ymS;
             cplx f = R->wpsi[j] * p1 * leg_diff(P2, s, y, ymS);
@@ -449,7 +486,7 @@ static int rules_init(rules *R, const orc_params *Q)
     if (Q->dim != 3 && Q->dim != 4) return ORC_EINVAL;
     if (Q->n_angular < 2) return ORC_EINVAL;
     if (Q->angular_rule == ORC_ANG_TANH_SINH && Q->n_angular % 2 == 0) return ORC_EINVAL;
-    if (Q->angular_rule < ORC_ANG_GL || Q->angular_rule > ORC_ANG_CHEB2) return ORC_EINVAL;
+    if (Q->angular_rule < ORC_ANG_GL || Q->angular_rule > ORC_ANG_EXACT) return ORC_EINVAL;
     if (Q->n_radial < 4 || Q->n_radial % 4) return ORC_EINVAL;
     if (!(Q->radial_scale > 0.0) || !(Q->detour_radius > 0.0)) return ORC_EINVAL;
     R->dim = Q->dim;
@@ -467,7 +504,9 @@ static int rules_init(rules *R, const orc_params *Q)
     R->cpsi = malloc(sizeof(double) * R->n_a);
     orc_gauss_legendre(R->n_r, R->gr_x, R->gr_w);
     orc_gauss_legendre(ns, R->gs_x, R->gs_w);
-    int rc = orc_angular_rule(Q->angular_rule, R->n_a, R->dim, R->cpsi, R->wpsi);
+    R->exact = Q->angular_rule == ORC_ANG_EXACT;
+    int rc = orc_angular_rule(R->exact ? ORC_ANG_GL : Q->angular_rule, R->n_a, R->dim, R->cpsi,
+                              R->wpsi);
     if (rc != ORC_OK) {
         rules_free(R);
         return rc;

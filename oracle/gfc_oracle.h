@@ -13,7 +13,8 @@ enum { ORC_OK = 0, ORC_EINVAL = -1, ORC_ENOMEM = -2 };
 enum { ORC_PROP_SCALAR = 0, ORC_PROP_CPAIR = 1, ORC_PROP_DRESSED = 2 };
 /* angular rules (Sect. 4): Gauss-Legendre in psi (default), tanh-sinh in
  * z = cos psi (the paper's), Gauss-Chebyshev of the first and second kind */
-enum { ORC_ANG_GL = 0, ORC_ANG_TANH_SINH = 1, ORC_ANG_CHEB1 = 2, ORC_ANG_CHEB2 = 3 };
+enum { ORC_ANG_GL = 0, ORC_ANG_TANH_SINH = 1, ORC_ANG_CHEB1 = 2, ORC_ANG_CHEB2 = 3,
+       ORC_ANG_EXACT = 4 /* the psi integral in closed form (no angular nodes) */ };
 
 typedef struct {
     int kind;

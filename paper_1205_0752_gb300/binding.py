@@ -17,7 +17,7 @@ GFC_ETIMEOUT, GFC_ECANCELED, GFC_EBUSY, GFC_ENOTFOUND = -5, -6, -7, -8
 GFC_PROP_SCALAR, GFC_PROP_CPAIR, GFC_PROP_DRESSED = 0, 1, 2
 GFC_FP64, GFC_MIXED, GFC_F32X2 = 0, 1, 2
 _PRECISION = {"fp64": GFC_FP64, "mixed": GFC_MIXED, "f32x2": GFC_F32X2}
-ANGULAR_RULES = {"gl": 0, "tanh-sinh": 1, "chebyshev1": 2, "chebyshev2": 3}
+ANGULAR_RULES = {"gl": 0, "tanh-sinh": 1, "chebyshev1": 2, "chebyshev2": 3, "exact": 4}
 
 
 class GfcError(RuntimeError):
@@ -154,7 +154,7 @@ def make_prop(spec) -> _Prop:
 def make_params(spec=None, **kw) -> _Params:
     """Defaults of gfc_params_default, overridden by ``spec``/keywords;
     ``precision`` and ``mixed_fallback`` may be 'fp64', 'mixed' or 'f32x2',
-    ``angular_rule`` 'gl', 'tanh-sinh', 'chebyshev1' or 'chebyshev2'."""
+    ``angular_rule`` 'gl', 'tanh-sinh', 'chebyshev1', 'chebyshev2' or 'exact'."""
     if isinstance(spec, _Params) and not kw:
         return spec
     lib = load_library()

@@ -400,9 +400,11 @@ static int build_tables(Tables &T)
     }
     // angular pairs: psi_j and pi - psi_j on [0, pi], weight w sin^(D-2) psi;
     // an odd rule's centre node psi = pi/2 pairs with itself at half weight
-    std::vector<double> az(T.n_a), aw(T.n_a);
-    angular_nodes(T.ang_rule, T.n_a, T.dim, az, aw);
-    int np = (T.n_a + 1) / 2;
+    // (none when the angular integral is taken in closed form)
+    const bool exact = T.ang_rule == GFC_ANG_EXACT;
+    std::vector<double> az(exact ? 0 : T.n_a), aw(exact ? 0 : T.n_a);
+    if (!exact) angular_nodes(T.ang_rule, T.n_a, T.dim, az, aw);
+    int np = exact ? 0 : (T.n_a + 1) / 2;
     T.t.resize(np);
     T.e.resize(np);
     T.g.resize(np);
@@ -538,7 +540,7 @@ static int check_params(const gfc_params *p)
         return fail(GFC_EINVAL, "n_radial must be a multiple of 4 in [4, 16384]");
     if (p->n_angular < 2 || p->n_angular > kMaxAngular)
         return fail(GFC_EINVAL, "n_angular must be in [2, 512]");
-    if (p->angular_rule < GFC_ANG_GAUSS_LEGENDRE || p->angular_rule > GFC_ANG_CHEBYSHEV2)
+    if (p->angular_rule < GFC_ANG_GAUSS_LEGENDRE || p->angular_rule > GFC_ANG_EXACT)
         return fail(GFC_EINVAL, "angular_rule must be a gfc_angular_rule");
     if (p->angular_rule == GFC_ANG_TANH_SINH && (p->n_angular % 2 == 0 || p->n_angular < 3))
         return fail(GFC_EINVAL, "the tanh-sinh rule needs an odd n_angular >= 3");
@@ -614,7 +616,8 @@ static void fill_kparams_tables(KParams &kp, const gfc_params *p, const Tables &
     kp.dim = p->dim;
     kp.n_r = p->n_radial;
     kp.n_s = p->n_radial / 4;
-    kp.npair = (p->n_angular + 1) / 2;
+    kp.npair = npair_of(p);
+    kp.ang_exact = p->angular_rule == GFC_ANG_EXACT;
     kp.rad64 = T.rad64;
     kp.rad32 = T.rad32;
     kp.seg64 = T.seg64;

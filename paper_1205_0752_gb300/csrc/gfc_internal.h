@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "gfc.h"
+
 namespace gfc {
 
 constexpr int kMaxRadial = 16384;
@@ -50,8 +52,9 @@ struct KParams {
     int dim;
     int n_r;             // radial nodes
     int n_s;             // nodes per detour segment (n_r / 4)
-    int npair;           // angular pairs (n_angular / 2)
+    int npair;           // angular pairs ((n_angular + 1) / 2; 0 with ang_exact)
     int mode;            // LaunchMode
+    int ang_exact;       // angular integral in closed form (GFC_ANG_EXACT)
     int use_grid;        // 1: x from the grid spec, 0: from x[]
     int64_t npts;
     // grid (Kernel 1)
@@ -154,6 +157,12 @@ int cuda_fail(cudaError_t e, const char *what);
 int check_params_c(const void *params);
 int check_grid_c(const void *grid);
 int make_prop_c(const void *prop, const void *params, PropConst &pc);
+// angular pairs of a parameter set (0 when the angular integral is exact)
+inline int npair_of(const gfc_params *p)
+{
+    return p->angular_rule == GFC_ANG_EXACT ? 0 : (p->n_angular + 1) / 2;
+}
+
 int get_tables_c(int dev, int n_r, int n_a, int dim, double L, int ang_rule, Tables **out,
                  size_t *bytes);
 void fill_kparams_c(KParams &kp, const void *params, const Tables &T, const PropConst &pc);

@@ -92,6 +92,8 @@ __device__ __forceinline__ float tsqrt(float x) { return sqrtf(x); }
 __device__ __forceinline__ double tsqrt(double x) { return sqrt(x); }
 __device__ __forceinline__ float tatan2(float y, float x) { return atan2f(y, x); }
 __device__ __forceinline__ double tatan2(double y, double x) { return atan2(y, x); }
+__device__ __forceinline__ float tlog(float x) { return logf(x); }
+__device__ __forceinline__ double tlog(double x) { return log(x); }
 
 // principal square root
 template <typename T>
@@ -560,6 +562,57 @@ __device__ __forceinline__ int pair_sums(const KParams &kp, const AngTab<T, tab_
     return rule < kp.nrule ? kp.rule_n[rule] : npair;
 }
 
+// The angular integral in closed form, the limit of every angular rule: half
+// of int_0^pi sin^(D-2) psi (v c - 1)/(1 - w c) dpsi, c = cos^2 psi (the half
+// matches the pair sums, which weight each +-psi pair once). With
+// (v c - 1)/(1 - w c) = -v/w + (v/w - 1)/(1 - w c):
+//   D = 4: int sin^2/(1 - w c) = pi/(1 + s), s = sqrt(1 - w), and the whole
+//          reduces to (pi/2)(v/(2(1 + s)) - 1)/(1 + s), free of cancellation;
+//   D = 3: int sin/(1 - w c) = 2 A, A = artanh(sqrt w)/sqrt w, giving
+//          (v - w) B1 - 1 with B1 = (A - 1)/w = sum_k>=1 w^(k-1)/(2k + 1)
+//          (the series for |w| < 0.1, the logarithms otherwise).
+// Principal branches: analytic off w in [1, inf), where the angular
+// integrand has its poles; the contours keep w off that half-line.
+template <typename T>
+__device__ __forceinline__ C<T> exact_S_impl(int dim, C<T> v, C<T> w)
+{
+    const T one = T(1);
+    if (dim == 4) {
+        C<T> s = csqrt_p(C<T>{one - w.r, -w.i});
+        C<T> r = cinv(C<T>{one + s.r, s.i});
+        C<T> u = T(0.5) * (v * r);
+        return T(0.5 * PI_D()) * (C<T>{u.r - one, u.i} * r);
+    }
+    C<T> B1;
+    if (cabs2(w) < T(0.01)) {
+        // sum_k>=1 w^(k-1)/(2k + 1) to rounding level for |w| < 0.1
+        B1 = C<T>{T(1.0 / 37.0), T(0)};
+        for (int k = 17; k >= 1; --k) B1 = C<T>{T(1) / T(2 * k + 1), T(0)} + w * B1;
+    } else {
+        C<T> z = csqrt_p(w);
+        // artanh z = (log(1 + z) - log(1 - z))/2, principal logarithms
+        C<T> p = {one + z.r, z.i}, m = {one - z.r, -z.i};
+        T lr = T(0.5) * (tlog(cabs2(p)) - tlog(cabs2(m)));
+        T li = tatan2(p.i, p.r) - tatan2(m.i, m.r);
+        C<T> at = T(0.5) * C<T>{lr, li};
+        C<T> A = at * cinv(z);
+        B1 = C<T>{A.r - one, A.i} * cinv(w);
+    }
+    C<T> vw = v - w;
+    C<T> r = vw * B1;
+    return C<T>{r.r - one, r.i};
+}
+template <typename T>
+__device__ __forceinline__ C<T> exact_S(int dim, C<T> v, C<T> w) { return exact_S_impl<T>(dim, v, w); }
+// double-float: evaluated in binary64 (a few operations per node)
+template <>
+__device__ __forceinline__ C<df> exact_S<df>(int dim, C<df> v, C<df> w)
+{
+    C<double> r = exact_S_impl<double>(dim, C<double>{(double)v.r, (double)v.i},
+                                       C<double>{(double)w.r, (double)w.i});
+    return C<df>{df(r.r), df(r.i)};
+}
+
 // Per-pass constants of one point, computed once and reused for every node.
 template <typename T, int NT>
 struct PassPre {
@@ -636,17 +689,34 @@ __device__ __forceinline__ C<T> node_value(const KParams &kp, const AngTab<T, ta
         if (want_mag) kap[s] = (cabs1(x) + cabs1(nd.y)) * rcp(cabs1(a));
     }
     T A[NT], B[NT];
-    npairs = pair_sums<T, NP, NT>(kp, tab, kp.npair, stab, srules, w, A, B, qmin) * pp.nt;
+    C<T> Sx[NT];
+    if (kp.ang_exact) {
+        qmin = T(1e30);
+#pragma unroll
+        for (int s = 0; s < NT; ++s) {
+            Sx[s] = exact_S<T>(kp.dim, v[s], w[s]);
+            if (sizeof(T) == 4) qmin = fmin(qmin, cabs2(C<T>{T(1) - w[s].r, -w[s].i}));
+            A[s] = B[s] = T(0);
+        }
+        npairs = 0;
+    } else {
+        npairs = pair_sums<T, NP, NT>(kp, tab, kp.npair, stab, srules, w, A, B, qmin) * pp.nt;
+    }
     const T Om1 = T(kp.Omega1), del = T(kp.delta);
     C<T> sum = {T(0), T(0)};
     T mag = T(0), magk = T(0);
 #pragma unroll
     for (int s = 0; s < NT; ++s) {
         if (s >= pp.nt) break;
-        C<T> T2 = {A[s] - w[s].r * B[s], w[s].i * B[s]};
-        C<T> lead = (del * nd.y - pp.omx[s]) * ia[s] - Om1 * w[s];
-        C<T> vw = (v[s] - w[s]) * w[s];
-        C<T> S = lead + vw * T2;
+        C<T> S;
+        if (kp.ang_exact) {
+            S = Sx[s];
+        } else {
+            C<T> T2 = {A[s] - w[s].r * B[s], w[s].i * B[s]};
+            C<T> lead = (del * nd.y - pp.omx[s]) * ia[s] - Om1 * w[s];
+            C<T> vw = (v[s] - w[s]) * w[s];
+            S = lead + vw * T2;
+        }
         // (1 + |y|)^2 P1(y) / (y + M2)
         C<T> pq = nd.sc * cinv(nd.y + pp.m2q[s]);
         C<T> p1;

@@ -174,7 +174,8 @@ double work_per_point(const Request &r, int arith)
     double nodes = r.params.n_radial;
     if (r.prop.kind != GFC_PROP_SCALAR) nodes *= 1.75;
     double terms = r.prop.kind == GFC_PROP_DRESSED ? 2.0 : 1.0;
-    double w = nodes * ((r.params.n_angular + 1) / 2) * terms;
+    // the closed-form angular integral costs about as much as four pairs
+    double w = nodes * std::max(npair_of(&r.params), 4) * terms;
     return arith == ARITH_F32 ? w : (arith == ARITH_DF ? w * kDfWeight : w * kFp64Weight);
 }
 
@@ -292,7 +293,7 @@ void issue_launches(gfc_server *s)
         for (int p = 0; p < (int)r->phases.size(); ++p) {
             const Phase &ph = r->phases[p];
             if (ph.end < 0 || ph.next >= ph.end) continue;
-            GroupKey k{ph.arith, (r->params.n_angular + 1) / 2, r->params.dim,
+            GroupKey k{ph.arith, npair_of(&r->params), r->params.dim,
                        r->prop.kind == GFC_PROP_DRESSED ? 1 : 0, ph.mode, r->params.angular_rule};
             groups[k].push_back({r, p});
         }

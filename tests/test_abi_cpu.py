@@ -47,7 +47,7 @@ def test_defaults():
 @pytest.mark.parametrize("bad", [dict(dim=2), dict(n_radial=6), dict(n_radial=20000),
                                  dict(n_angular=1), dict(n_angular=1024), dict(mu2=-1.0),
                                  dict(angular_rule="tanh-sinh", n_angular=64),
-                                 dict(angular_rule=4),
+                                 dict(angular_rule=5),
                                  dict(radial_scale=-1.0), dict(precision=7),
                                  dict(mixed_rtol=-1.0), dict(mixed_fallback="mixed")])
 def test_bad_params_rejected_on_the_host(bad):

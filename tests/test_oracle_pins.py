@@ -239,6 +239,50 @@ def test_angular_rules_reach_the_closed_form(rule, n, tol):
     assert e49[0] < 1e-13 and e49[1] > np.max(np.abs(G - ref)[1] / np.abs(ref[1]))
 
 
+@pytest.mark.parametrize("dim", [3, 4])
+@pytest.mark.parametrize("prop", [{"kind": "scalar", "m2": 1.0},
+                                  {"kind": "cpair", "mk2": 0.5j, "mq2": -0.5j},
+                                  {"kind": "dressed", "a": 1.0, "b": 0.5, "c": 2.0}])
+def test_exact_angular_is_the_limit_of_the_rules(prop, dim):
+    """The closed-form psi integral (written from int sin^(D-2)/(A - B cos psi))
+    is the n -> infinity limit of the Gauss-Legendre rule, on rays and detours."""
+    xs = np.array([2 + 1j, -2 + 3j, 0.5 - 2j, -1 - 1.5j, 3 + 0.2j])
+    mu2 = 0.0 if prop["kind"] == "cpair" else 1.0
+    base = dict(dim=dim, mu2=mu2, n_radial=512)
+    Ge = oracle.eval_points(prop, dict(base, n_angular=2, angular_rule="exact"), xs)
+    Gq = oracle.eval_points(prop, dict(base, n_angular=1024), xs)
+    assert np.max(np.abs(Ge - Gq) / np.abs(Gq)) < 1e-11
+
+
+@pytest.mark.parametrize("dim", [3, 4])
+def test_exact_angular_closes_the_near_axis_gap(dim):
+    """Next to the negative real axis the angular rule's error dominates (the
+    integrand nearly pinches); with the psi integral in closed form the radial
+    rule alone decides, and refining it reaches the closed form."""
+    prop = {"kind": "scalar", "m2": 1.0}
+    xs = np.array([-2 + 0.0625j, -6 + 0.0625j])
+    ref = np.array([G_exact(prop, x, dim, 1.0) for x in xs])
+    gl = oracle.eval_points(prop, dict(dim=dim, mu2=1.0, n_radial=8192, n_angular=256), xs)
+    ex = oracle.eval_points(prop, dict(dim=dim, mu2=1.0, n_radial=8192, n_angular=2,
+                                       angular_rule="exact"), xs)
+    e_gl = np.abs(gl - ref) / np.abs(ref)
+    e_ex = np.abs(ex - ref) / np.abs(ref)
+    assert np.all(e_gl > 1e-3) and np.all(e_ex < 1e-8)
+
+
+def test_exact_angular_dressed_closed_form():
+    """The dressed propagator with the closed-form psi integral against its
+    partial-fraction closed forms (D = 4 and 3, b = 0 and b > 0)."""
+    for dim in (3, 4):
+        for abc in ((1.0, 0.0, 2.0), (1.0, 0.5, 2.0)):
+            prop = {"kind": "dressed", "a": abc[0], "b": abc[1], "c": abc[2]}
+            xs = np.array([1.5 + 1j, -1 + 2j, 0.5 - 3j])
+            ref = np.array([G_exact(prop, x, dim, 1.0) for x in xs])
+            G = oracle.eval_points(prop, dict(dim=dim, mu2=1.0, n_radial=2048, n_angular=2,
+                                              angular_rule="exact"), xs)
+            assert np.max(np.abs(G - ref) / np.abs(ref)) < 1e-9, (dim, abc)
+
+
 def test_condition_number_reported():
     """kappa = sum|terms|/|sum| grows as x approaches the negative real axis,
     where the angular integrand nearly pinches."""
