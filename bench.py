@@ -346,6 +346,23 @@ def run_gfc(args):
             tex, _ = timed(parex, 1, 1)
             exact_rule[f"{prec}_nr{nr}"] = ws * npts_step / tex
 
+    # ---- Step 3 diagnostics: region-1 map and the y-plane map of B --------
+    diag = {}
+    xg = gfc.grid_points((*rect, side, side), stream=stream).reshape(-1)
+    for name, fn in (("region_map_points_per_s", lambda: gfc.region_map(props[1], xg, stream=stream)),
+                     ("angular_map_gl256_y_per_s",
+                      lambda: gfc.angular_map(props[1], par64, -2.0 + 1.0j, xg, stream=stream)),
+                     ("angular_map_exact_y_per_s",
+                      lambda: gfc.angular_map(props[1], gfc.make_params(angular_rule="exact"),
+                                              -2.0 + 1.0j, xg, stream=stream))):
+        fn()
+        a_ev, b_ev = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a_ev.record(stream)
+        fn()
+        b_ev.record(stream)
+        torch.cuda.synchronize()
+        diag[name] = xg.numel() / (a_ev.elapsed_time(b_ev) / 1e3)
+
     # ---- end to end through the host-buffer C-ABI call --------------------
     import oracle  # grid points of the block, written by the oracle's Kernel 1
     xh = torch.from_numpy(oracle.grid_points(*rect, side, side)).pin_memory()
@@ -420,6 +437,8 @@ def run_gfc(args):
         "exact_angular": dict({"rule": "psi integral in closed form (limit of every angular "
                                          "rule); radial Gauss-Legendre n_radial as named",
                                "unit": "points/s"}, **exact_rule),
+        "diagnostics": dict({"grid": f"{side}x{side} x (region map) or y (map of B at x = -2 + i)",
+                             "propagator": "bubble m = 1"}, **diag),
         "e2e": {"value": e2e_value, "unit": "points/s", "h2d_bytes_per_step": 3 * 16 * side * side,
                 "d2h_bytes_per_step": 3 * 16 * side * side},
     }

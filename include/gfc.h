@@ -213,6 +213,30 @@ int gfc_eval_points_host(const gfc_propagator *prop, const gfc_params *params,
 int gfc_eval_points_noalloc(const gfc_propagator *prop, const gfc_params *params,
                             const double *x, int64_t npts, double *G, void *stream);
 
+/* Step 3 diagnostics (Sect. 5, Figs. 1-2), binary64.
+ *
+ * gfc_angular_map: the angular integral of the (p-k) leg as given (no
+ * relabelling), B(x, y) = int_0^pi sin^(D-2) psi [P2(s) - P2(y)] dpsi with
+ * s = x + y - 2 sqrt(x) sqrt(y) cos psi, at one external x = x_re + i x_im
+ * and ny complex y (DEVICE arrays of complex128, y in, B out), with the
+ * params' angular rule (or in closed form, GFC_ANG_EXACT). Evaluated over a
+ * grid of y it is the density plot of Fig. 1: B jumps across the branch cut
+ * of eq. 25; a y on a node of the rule's pole set gives inf/NaN. Uses dim,
+ * n_angular and angular_rule of params (the radial fields are validated but
+ * unused). GFC_EINVAL for bad params or pointers. */
+int gfc_angular_map(const gfc_propagator *prop, const gfc_params *params, double x_re,
+                    double x_im, const double *y, int64_t ny, double *B, void *stream);
+
+/* gfc_region_map: region 1 of Fig. 2. For each of npts external x (DEVICE
+ * complex128), free_out[i] (DEVICE int32) = 1 if the branch cut of B(x, .)
+ * -- the curve y = (sqrt(x) cos th +- sqrt(-x sin^2 th - M2))^2, th in
+ * [0, pi], of eqs. 24-25 for each pole s = -M2 of the (p-k) leg as given --
+ * does not cross the positive real y-axis, so the original contour along it
+ * can be kept; else 0. The curve is traced on 4096 samples of th, so points
+ * within about that resolution of the region's boundary may go either way. */
+int gfc_region_map(const gfc_propagator *prop, const double *x, int64_t npts,
+                   int32_t *free_out, void *stream);
+
 /* Counters of the last gfc_eval_* call made on this thread; waits for the
  * work of that call to finish (the counts are read from the device). */
 int gfc_last_stats(gfc_eval_stats *out);

@@ -71,6 +71,11 @@ def _bind(path: str):
     lib.orc_angular_rule.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
                                      ctypes.c_void_p]
     lib.orc_gauss_legendre.restype = ctypes.c_int
+    lib.orc_angular_map.argtypes = [ctypes.POINTER(_Prop), ctypes.POINTER(_Params),
+                                    ctypes.c_double, ctypes.c_double, ctypes.c_void_p,
+                                    ctypes.c_long, ctypes.c_void_p]
+    lib.orc_region_map.argtypes = [ctypes.POINTER(_Prop), ctypes.c_void_p, ctypes.c_long,
+                                   ctypes.c_void_p]
     return lib
 
 
@@ -176,6 +181,31 @@ def angular_rule(rule, n: int, dim: int):
     if lib.orc_angular_rule(r, n, dim, z.ctypes.data, w.ctypes.data) != 0:
         raise ValueError("bad angular rule, order or dimension")
     return z, w
+
+
+def angular_map(prop: dict, params: dict, x: complex, y):
+    """B(x, y) = int_0^pi sin^(D-2) psi [P2(s) - P2(y)] dpsi of the (p-k) leg
+    as given, at complex y (Sect. 5, Fig. 1)."""
+    lib = _load()
+    y = np.ascontiguousarray(np.asarray(y, dtype=np.complex128).ravel())
+    B = np.empty_like(y)
+    rc = lib.orc_angular_map(ctypes.byref(_prop(prop)), ctypes.byref(_params(params)),
+                             float(np.real(x)), float(np.imag(x)), y.ctypes.data, y.size,
+                             B.ctypes.data)
+    if rc != 0:
+        raise ValueError(f"orc_angular_map failed ({rc})")
+    return B
+
+
+def region_map(prop: dict, x):
+    """1 where the real-axis y contour is free of the angular integral's cut
+    (region 1 of Fig. 2), else 0."""
+    lib = _load()
+    x = np.ascontiguousarray(np.asarray(x, dtype=np.complex128).ravel())
+    out = np.empty(x.size, dtype=np.int32)
+    if lib.orc_region_map(ctypes.byref(_prop(prop)), x.ctypes.data, x.size, out.ctypes.data) != 0:
+        raise ValueError("orc_region_map failed")
+    return out
 
 
 def gauss_legendre(n: int):

@@ -641,3 +641,104 @@ int orc_grid_points(double re0, double re1, double im0, double im1, int m, int n
         }
     return ORC_OK;
 }
+
+/* ---------------------------------------------------------------------------
+ * Step 3 diagnostics (Sect. 5, Figs. 1-2).
+ * ------------------------------------------------------------------------- */
+/* the (p-k) leg as given by the caller (no relabelling) */
+static int given_q_leg(const orc_prop *P, leg *L)
+{
+    if (P->kind == ORC_PROP_SCALAR) { leg l = {PL_POLE, P->m2, 0, 0, 0}; *L = l; return ORC_OK; }
+    if (P->kind == ORC_PROP_CPAIR) {
+        leg l = {PL_POLE, P->mq2_re + I * P->mq2_im, 0, 0, 0};
+        *L = l;
+        return ORC_OK;
+    }
+    if (P->kind == ORC_PROP_DRESSED && 4.0 * P->c - P->b * P->b > 0.0) {
+        leg l = {PL_DRESSED, 0, P->a, P->b, P->c};
+        *L = l;
+        return ORC_OK;
+    }
+    return ORC_EINVAL;
+}
+
+int orc_angular_map(const orc_prop *P, const orc_params *Q, double xr, double xi,
+                    const double *y, long ny, double *B)
+{
+    leg L;
+    if (given_q_leg(P, &L) != ORC_OK || ny < 0) return ORC_EINVAL;
+    rules R;
+    int rc = rules_init(&R, Q);
+    if (rc != ORC_OK) return rc;
+    cplx x = xr + I * xi;
+    for (long i = 0; i < ny; ++i) {
+        cplx yy = y[2 * i] + I * y[2 * i + 1];
+        cplx b;
+        if (R.exact) {
+            b = leg_angular(&L, R.dim, x, yy);
+        } else {
+            /* the plain sum over the rule's nodes; only x y enters s */
+            cplx sxy = csqrt(x * yy), py = leg_eval(&L, yy);
+            nsum acc = {0, 0, 0, 0};
+            for (int j = 0; j < R.n_a; ++j) {
+                cplx s = x + yy - 2.0 * sxy * R.cpsi[j];
+                nsum_add(&acc, R.wpsi[j] * (leg_eval(&L, s) - py));
+            }
+            b = nsum_get(&acc);
+        }
+        B[2 * i] = creal(b);
+        B[2 * i + 1] = cimag(b);
+    }
+    rules_free(&R);
+    return ORC_OK;
+}
+
+/* Does some y > 0 give w = 4 x y/(x + y + M2)^2 real and >= 1 (then
+ * cos^2 psi = 1/w puts a pole of 1/(s + M2) on the angular range)? The scan
+ * y = u/(1 - u), u on a uniform grid of (0, 1), looks for sign changes of
+ * Im w and interpolates Re w there. */
+static int pole_obstructs(cplx x, cplx M2)
+{
+    const int K = 16384;
+    /* x and M2 real: w is real for every real y and the pole condition
+     * cos psi = a/b (b = 2 sqrt(x y)) holds only where a = x + y + M2 = 0,
+     * i.e. at y = -x - M2 when that is positive (the cut side of the axis) */
+    if (cimag(x) == 0.0 && cimag(M2) == 0.0) return creal(x) < 0.0 && -creal(x) - creal(M2) > 0.0;
+    double pim = 0.0, pre = 0.0;
+    for (int k = 0; k < K; ++k) {
+        double u = (k + 0.5) / K, yv = u / (1.0 - u);
+        cplx a = x + yv + M2, w = 4.0 * x * yv / (a * a);
+        double wi = cimag(w), wr = creal(w);
+        if (k > 0 && ((pim < 0.0 && wi >= 0.0) || (pim > 0.0 && wi <= 0.0))) {
+            double f = pim / (pim - wi);
+            if (pre + f * (wr - pre) >= 1.0) return 1;
+        }
+        pim = wi;
+        pre = wr;
+    }
+    return 0;
+}
+
+int orc_region_map(const orc_prop *P, const double *x, long n, int *free_out)
+{
+    leg L;
+    if (given_q_leg(P, &L) != ORC_OK || n < 0) return ORC_EINVAL;
+    cplx M[2];
+    int nm = 1;
+    if (L.form == PL_POLE) {
+        M[0] = L.M2;
+    } else {
+        double disc = 4.0 * L.c - L.b * L.b;
+        cplx r1 = 0.5 * (-L.b + I * sqrt(disc));
+        M[0] = -r1;
+        M[1] = -conj(r1);
+        nm = 2;
+    }
+    for (long i = 0; i < n; ++i) {
+        cplx xx = x[2 * i] + I * x[2 * i + 1];
+        int obstructed = 0;
+        for (int t = 0; t < nm && !obstructed; ++t) obstructed = pole_obstructs(xx, M[t]);
+        free_out[i] = !obstructed;
+    }
+    return ORC_OK;
+}

@@ -42,6 +42,16 @@ int orc_angular_rule(int rule, int n, int dim, double *z, double *w);
 int orc_eval_points(const orc_prop *P, const orc_params *Q, const double *x, long npts,
                     double *G, double *kappa, int nthreads);
 int orc_grid_points(double re0, double re1, double im0, double im1, int m, int n, double *x);
+/* Step 3 diagnostics (Sect. 5, Figs. 1-2). The angular integral of the
+ * (p-k) leg as given, B(x, y) = int_0^pi sin^(D-2) psi [P2(s) - P2(y)] dpsi,
+ * s = x + y - 2 sqrt(x y) cos psi, at one x and ny complex y (interleaved),
+ * with Q's angular rule (or in closed form). */
+int orc_angular_map(const orc_prop *P, const orc_params *Q, double xr, double xi,
+                    const double *y, long ny, double *B);
+/* Region 1 of Fig. 2: free[i] = 1 if no y on the positive real axis puts a
+ * pole of the angular integrand on [0, pi] (the real-axis contour can be
+ * kept), else 0. Found by scanning w = 4 x y/(x + y + M2)^2 along y > 0. */
+int orc_region_map(const orc_prop *P, const double *x, long n, int *free_out);
 
 #ifdef __cplusplus
 }

@@ -94,6 +94,9 @@ _SIGS = {
     "gfc_server_cancel": ([_P, ctypes.c_uint64], ctypes.c_int),
     "gfc_server_stats": ([_P, ctypes.POINTER(_ServerStats)], ctypes.c_int),
     "gfc_server_destroy": ([_P], ctypes.c_int),
+    "gfc_angular_map": ([ctypes.POINTER(_Prop), ctypes.POINTER(_Params), ctypes.c_double,
+                         ctypes.c_double, _P, ctypes.c_int64, _P, _P], ctypes.c_int),
+    "gfc_region_map": ([ctypes.POINTER(_Prop), _P, ctypes.c_int64, _P, _P], ctypes.c_int),
 }
 
 _lib = None
@@ -366,3 +369,30 @@ class Server:
 
     def __exit__(self, *exc):
         self.close()
+
+
+def angular_map(prop, params, x, y, out=None, stream=None):
+    """B(x, y) of gfc_angular_map at one complex x for the complex128 CUDA
+    tensor y (Sect. 5, Fig. 1)."""
+    import torch
+    lib = load_library()
+    y = y.contiguous()
+    B = out if out is not None else torch.empty_like(y)
+    _check(lib.gfc_angular_map(ctypes.byref(make_prop(prop)), ctypes.byref(make_params(params)),
+                               float(complex(x).real), float(complex(x).imag),
+                               ctypes.c_void_p(y.data_ptr()), y.numel(),
+                               ctypes.c_void_p(B.data_ptr()), _stream_ptr(stream)),
+           "gfc_angular_map")
+    return B
+
+
+def region_map(prop, x, out=None, stream=None):
+    """int32 CUDA tensor: 1 where x lies in region 1 of Fig. 2 (gfc_region_map)."""
+    import torch
+    lib = load_library()
+    x = x.contiguous()
+    F = out if out is not None else torch.empty(x.shape, dtype=torch.int32, device=x.device)
+    _check(lib.gfc_region_map(ctypes.byref(make_prop(prop)), ctypes.c_void_p(x.data_ptr()),
+                              x.numel(), ctypes.c_void_p(F.data_ptr()), _stream_ptr(stream)),
+           "gfc_region_map")
+    return F

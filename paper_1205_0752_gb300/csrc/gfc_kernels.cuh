@@ -574,15 +574,19 @@ __device__ __forceinline__ int pair_sums(const KParams &kp, const AngTab<T, tab_
 // Principal branches: analytic off w in [1, inf), where the angular
 // integrand has its poles; the contours keep w off that half-line.
 template <typename T>
+__device__ __forceinline__ C<T> exact_S4(C<T> v, C<T> w)
+{
+    const T one = T(1);
+    C<T> s = csqrt_p(C<T>{one - w.r, -w.i});
+    C<T> r = cinv(C<T>{one + s.r, s.i});
+    C<T> u = T(0.5) * (v * r);
+    return T(0.5 * PI_D()) * (C<T>{u.r - one, u.i} * r);
+}
+template <typename T>
 __device__ __forceinline__ C<T> exact_S_impl(int dim, C<T> v, C<T> w)
 {
     const T one = T(1);
-    if (dim == 4) {
-        C<T> s = csqrt_p(C<T>{one - w.r, -w.i});
-        C<T> r = cinv(C<T>{one + s.r, s.i});
-        C<T> u = T(0.5) * (v * r);
-        return T(0.5 * PI_D()) * (C<T>{u.r - one, u.i} * r);
-    }
+    if (dim == 4) return exact_S4<T>(v, w);
     C<T> B1;
     if (cabs2(w) < T(0.01)) {
         // sum_k>=1 w^(k-1)/(2k + 1) to rounding level for |w| < 0.1
@@ -604,10 +608,11 @@ __device__ __forceinline__ C<T> exact_S_impl(int dim, C<T> v, C<T> w)
 }
 template <typename T>
 __device__ __forceinline__ C<T> exact_S(int dim, C<T> v, C<T> w) { return exact_S_impl<T>(dim, v, w); }
-// double-float: evaluated in binary64 (a few operations per node)
+// double-float: D = 4 natively; D = 3 (logarithms) evaluated in binary64
 template <>
 __device__ __forceinline__ C<df> exact_S<df>(int dim, C<df> v, C<df> w)
 {
+    if (dim == 4) return exact_S4<df>(v, w);
     C<double> r = exact_S_impl<double>(dim, C<double>{(double)v.r, (double)v.i},
                                        C<double>{(double)w.r, (double)w.i});
     return C<df>{df(r.r), df(r.i)};

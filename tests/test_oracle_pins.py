@@ -283,6 +283,56 @@ def test_exact_angular_dressed_closed_form():
             assert np.max(np.abs(G - ref) / np.abs(ref)) < 1e-9, (dim, abc)
 
 
+@pytest.mark.parametrize("m2", [0.25, 1.0])
+def test_region_map_is_the_parabola(m2):
+    """Region 1 of Fig. 2 for a real mass: the real-axis y contour is free of
+    the angular integral's cut exactly inside Im^2 x < 4 m^2 (Re x + m^2), the
+    parabola of the figure (found here from the pole condition w = 4 x y/
+    (x + y + m^2)^2 >= 1 real on y > 0)."""
+    re = np.linspace(-9.9, 4.9, 75)
+    im = np.linspace(-4.9, 4.9, 61)
+    x = (re[:, None] + 1j * im[None, :]).ravel()
+    got = oracle.region_map({"kind": "scalar", "m2": m2}, x)
+    par = (x.imag ** 2 < 4 * m2 * (x.real + m2)).astype(np.int32)
+    far = np.abs(x.imag ** 2 - 4 * m2 * (x.real + m2)) > 0.02
+    assert np.array_equal(got[far], par[far])
+    assert 0.1 < got.mean() < 0.9
+
+
+@pytest.mark.parametrize("dim", [3, 4])
+@pytest.mark.parametrize("prop", [{"kind": "scalar", "m2": 1.0},
+                                  {"kind": "cpair", "mk2": 0.5j, "mq2": -0.5j},
+                                  {"kind": "dressed", "a": 1.0, "b": 0.5, "c": 2.0}])
+def test_angular_map_rule_converges_to_closed_form(prop, dim):
+    """B(x, y) by the plain sum over a 1024-node rule against the closed form
+    at y away from the cut (Fig. 1's integral B)."""
+    x = 1.5 + 0.5j
+    y = np.array([0.3 + 0.1j, 2.0 - 1.0j, 5.0 + 3.0j, 0.05 + 0.02j, 10.0 - 0.5j])
+    q = oracle.angular_map(prop, dict(dim=dim, n_radial=4, n_angular=1024), x, y)
+    e = oracle.angular_map(prop, dict(dim=dim, n_radial=4, n_angular=2, angular_rule="exact"),
+                           x, y)
+    assert np.max(np.abs(q - e) / np.abs(e)) < 1e-11
+
+
+def test_angular_map_jumps_across_the_cut():
+    """Across the branch cut of eq. 25 B is discontinuous; along it and away
+    from it B is continuous (the paper's example, Fig. 1)."""
+    prop = {"kind": "cpair", "mk2": 0.5j, "mq2": -0.5j}
+    par = dict(dim=4, n_radial=4, n_angular=2, angular_rule="exact")
+    x = -2.0 + 1.0j
+    th = 1.1
+    k = np.sqrt(x) * np.cos(th) + np.sqrt(-x * np.sin(th) ** 2 + 0.5j)   # eq. 24, s = -Mq2
+    yc = k ** 2                                                           # eq. 25
+    dk = np.sqrt(x) * np.cos(th + 1e-4) + np.sqrt(-x * np.sin(th + 1e-4) ** 2 + 0.5j)
+    tang = dk ** 2 - yc
+    nrm = 1j * tang / abs(tang)
+    eps = 1e-7
+    across = oracle.angular_map(prop, par, x, [yc + eps * nrm, yc - eps * nrm])
+    along = oracle.angular_map(prop, par, x, [yc + eps * nrm, yc + eps * nrm + 1e-6 * tang / abs(tang)])
+    assert abs(across[0] - across[1]) > 1e-2 * abs(across[0])
+    assert abs(along[0] - along[1]) < 1e-4 * abs(along[0])
+
+
 def test_condition_number_reported():
     """kappa = sum|terms|/|sum| grows as x approaches the negative real axis,
     where the angular integrand nearly pinches."""
