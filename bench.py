@@ -346,6 +346,14 @@ def run_gfc(args):
             tex, _ = timed(parex, 1, 1)
             exact_rule[f"{prec}_nr{nr}"] = ws * npts_step / tex
 
+    # ---- near-axis accuracy: closed-form angle + clustered radial rule -----
+    clustered = {}
+    for prec in ("fp64", "f32x2", "mixed"):
+        parcl = gfc.make_params(dim=4, mu2=1.0, n_radial=NR, n_angular=2, angular_rule="exact",
+                                radial_rule="clustered", precision=prec)
+        tcl, _ = timed(parcl, 1, 1)
+        clustered[prec] = ws * npts_step / tcl
+
     # ---- Step 3 diagnostics: region-1 map and the y-plane map of B --------
     diag = {}
     xg = gfc.grid_points((*rect, side, side), stream=stream).reshape(-1)
@@ -437,6 +445,9 @@ def run_gfc(args):
         "exact_angular": dict({"rule": "psi integral in closed form (limit of every angular "
                                          "rule); radial Gauss-Legendre n_radial as named",
                                "unit": "points/s"}, **exact_rule),
+        "clustered_radial": dict({"rule": "closed-form angle, radial rule sinh-clustered at the "
+                                          "pole nearest the ray (n_radial 2048)",
+                                  "unit": "points/s"}, **clustered),
         "diagnostics": dict({"grid": f"{side}x{side} x (region map) or y (map of B at x = -2 + i)",
                              "propagator": "bubble m = 1"}, **diag),
         "e2e": {"value": e2e_value, "unit": "points/s", "h2d_bytes_per_step": 3 * 16 * side * side,

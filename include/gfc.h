@@ -41,7 +41,7 @@ extern "C" {
 #endif
 
 #define GFC_VERSION_MAJOR 1
-#define GFC_VERSION_MINOR 2
+#define GFC_VERSION_MINOR 3
 
 enum {
     GFC_OK = 0,
@@ -102,6 +102,22 @@ typedef enum {
                                     n_angular is ignored                       */
 } gfc_angular_rule;
 
+/* Radial rule of the rays that start at q = 0 (Step 3; the paper uses
+ * Gauss-Legendre and notes that contours close to singular structures need
+ * many nodes, Sect. 4). */
+typedef enum {
+    GFC_RAD_MAPPED = 0,     /* n_radial Gauss-Legendre nodes on |q| = L t/(1-t)
+                               (default)                                       */
+    GFC_RAD_CLUSTERED = 1   /* when a pole +-sqrt(y_p) of the propagator lies
+                               within ~37 degrees of the ray (distance d below
+                               0.75 of its projection c on the ray): n_radial/4
+                               nodes on each of [0, c] and [c, 2c], mapped by
+                               |q| = c + d sinh(s), then n_radial/2 on the
+                               mapped half-line from 2c; else as MAPPED. With
+                               GFC_ANG_EXACT this resolves the points next to
+                               the negative real axis beyond threshold.       */
+} gfc_radial_rule;
+
 typedef struct {
     int dim;               /* 3 or 4                                           */
     double mu2;            /* subtraction point, real, >= 0; G(mu2) = 0        */
@@ -128,6 +144,7 @@ typedef struct {
                               ~48 bits, 2-3x the GB300's FP64 rate) or
                               GFC_FP64                                          */
     int angular_rule;      /* gfc_angular_rule (default Gauss-Legendre)        */
+    int radial_rule;       /* gfc_radial_rule (default mapped half-line)       */
 } gfc_params;
 
 /* Cell-centred grid of Kernel 1 (Sect. 4): x_ij = re0 + (i + 1/2)(re1-re0)/m
@@ -159,7 +176,7 @@ int gfc_version(int *major, int *minor);
 
 /* Defaults: D = 4, mu2 = 1, 2048 x 256 nodes, L = 1, r = 0.1, FP64,
  * cut_band 0.05, pinch_angle 0, mixed_rtol 1e-6, mixed_fallback F32X2,
- * angular_rule Gauss-Legendre. */
+ * angular_rule Gauss-Legendre, radial_rule mapped. */
 int gfc_params_default(gfc_params *p);
 
 /* Steps 4-5 on caller-given points: x and G are DEVICE arrays of npts
@@ -204,7 +221,8 @@ int gfc_eval_points_host(const gfc_propagator *prop, const gfc_params *params,
  * 150 KB, so the call allocates nothing (no cudaMalloc, cudaFree or
  * allocating library call); x and G are the caller's DEVICE arrays as for
  * gfc_eval_points. Limits: precision GFC_FP64, n_radial <= 4096, even
- * n_angular <= 512, the Gauss-Legendre angular rule; anything else gives
+ * n_angular <= 512, the Gauss-Legendre angular rule and the mapped radial
+ * rule; anything else gives
  * GFC_EINVAL. The array is
  * shared by every call on a device and keeps the last call's contents: calls
  * that overlap on the GPU (other streams or host threads) race on it. The

@@ -36,10 +36,12 @@ class _Params(ctypes.Structure):
     _fields_ = [("dim", ctypes.c_int), ("mu2", ctypes.c_double),
                 ("n_radial", ctypes.c_int), ("n_angular", ctypes.c_int),
                 ("radial_scale", ctypes.c_double), ("detour_radius", ctypes.c_double),
-                ("angular_rule", ctypes.c_int)]
+                ("angular_rule", ctypes.c_int), ("radial_rule", ctypes.c_int)]
 
 # angular rules (Sect. 4)
 ANGULAR_RULES = {"gl": 0, "tanh-sinh": 1, "chebyshev1": 2, "chebyshev2": 3, "exact": 4}
+# radial rules of the rays from q = 0
+RADIAL_RULES = {"mapped": 0, "clustered": 1}
 
 
 def _compile(out: str, defines=()) -> None:
@@ -133,6 +135,8 @@ def _params(par: dict) -> _Params:
     q.detour_radius = float(par.get("detour_radius", 0.1))
     r = par.get("angular_rule", 0)
     q.angular_rule = ANGULAR_RULES[r] if isinstance(r, str) else int(r)
+    r = par.get("radial_rule", 0)
+    q.radial_rule = RADIAL_RULES[r] if isinstance(r, str) else int(r)
     return q
 
 

@@ -160,11 +160,67 @@ typedef struct {
     double L, r_detour;
     double *gr_x, *gr_w;     /* GL on [-1,1], n_r nodes (radial) */
     double *gs_x, *gs_w;     /* GL on [-1,1], n_r/4 nodes (detour segments) */
+    double *gt_x, *gt_w;     /* GL on [-1,1], n_r/2 nodes (clustered rule's tail) */
+    int radial_rule;
+    cplx ppoles[4];          /* poles of the propagator as given (y-plane) */
+    int nppoles;
     double *psi, *wpsi;      /* angular: psi_j, w_j sin^(D-2) psi_j */
     double *cpsi;            /* cos psi_j */
     int exact;               /* psi integral in closed form */
     double K_D;
 } rules;
+
+/* The clustered radial rule (near-axis accuracy): the propagator's poles y_p
+ * give q-plane points +-sqrt(y_p); the one closest in angle to the ray
+ * arg q = theta, with d < 0.75 c (within ~37 degrees; a reading: the paper
+ * gives no rule), has projection c and distance d from the ray. The ray then takes n_r/4 GL nodes on each of [0, c] and [c, 2c],
+ * mapped by |q| = c + d sinh(s) (s from -asinh(c/d) to 0, and from 0 to
+ * asinh(c/d)), which packs nodes within ~d of the near-singular point, and
+ * n_r/2 GL nodes on the mapped half-line |q| = 2c + L t/(1-t). Returns 0 when
+ * no pole qualifies (the plain mapped ray is used). */
+static int cluster_point(const rules *R, double theta, double *c, double *d)
+{
+    cplx e = cexp(-I * theta);
+    double best = 1.0;
+    int found = 0;
+    for (int i = 0; i < R->nppoles; ++i) {
+        for (int sg = -1; sg <= 1; sg += 2) {
+            cplx z = sg * csqrt(R->ppoles[i]) * e;
+            double rs = creal(z), ds = fabs(cimag(z));
+            if (rs > 0.0 && ds < 0.75 * rs && ds / rs < best) {
+                best = ds / rs;
+                *c = rs;
+                *d = ds;
+                found = 1;
+            }
+        }
+    }
+    if (found && *d < 1e-12 * *c) *d = 1e-12 * *c;
+    return found;
+}
+
+static void add_ray_clustered(nodes *N, const rules *R, double theta, double c, double d)
+{
+    cplx e = cexp(I * theta);
+    int ns = R->n_r / 4, nt = R->n_r / 2;
+    double eta = asinh(c / d);
+    for (int panel = 0; panel < 2; ++panel) {
+        for (int k = 0; k < ns; ++k) {
+            double t = 0.5 * (R->gs_x[k] + 1.0), wt = 0.5 * R->gs_w[k];
+            double sv = panel == 0 ? eta * (t - 1.0) : eta * t;
+            double rho = c + d * sinh(sv), drho = d * cosh(sv) * eta * wt;
+            cplx q = rho * e;
+            nodes_push(N, q * q, 2.0 * q * e * drho, q);
+        }
+    }
+    for (int k = 0; k < nt; ++k) {
+        double t = 0.5 * (R->gt_x[k] + 1.0), wt = 0.5 * R->gt_w[k];
+        double rho = 2.0 * c + R->L * t / (1.0 - t);
+        double drho = R->L / ((1.0 - t) * (1.0 - t)) * wt;
+        cplx q = rho * e;
+        nodes_push(N, q * q, 2.0 * q * e * drho, q);
+    }
+}
 
 /* q-ray from |q| = rho0 to infinity along arg q = theta (so arg y = 2 theta):
  * |q| = rho0 + L t/(1-t), t = GL on (0,1); y = q^2, dy = 2 q dq. */
@@ -358,8 +414,13 @@ static void term_contour(nodes *N, const rules *R, cplx x, const leg *P1, const 
         ray_distance(-P1->M2, phi) < 2.0 * R->r_detour && cimag(-P1->M2) * cimag(x) > 0.0)
         theta = NAN;
     N->n = 0;
-    if (!isnan(theta)) add_ray(N, R, theta, 0.0);
-    else               add_detour(N, R, x, -P1->M2);
+    double c, d;
+    if (!isnan(theta) && R->radial_rule == ORC_RAD_CLUSTERED && cluster_point(R, theta, &c, &d))
+        add_ray_clustered(N, R, theta, c, d);
+    else if (!isnan(theta))
+        add_ray(N, R, theta, 0.0);
+    else
+        add_detour(N, R, x, -P1->M2);
 }
 
 static int G0_point(const orc_prop *P, const rules *R, cplx x, cplx *G0, double *kappa,
@@ -476,7 +537,7 @@ int orc_angular_rule(int rule, int n, int dim, double *z, double *w)
  * ------------------------------------------------------------------------- */
 static void rules_free(rules *R)
 {
-    free(R->gr_x); free(R->gr_w); free(R->gs_x); free(R->gs_w);
+    free(R->gr_x); free(R->gr_w); free(R->gs_x); free(R->gs_w); free(R->gt_x); free(R->gt_w);
     free(R->psi); free(R->wpsi); free(R->cpsi);
 }
 
@@ -487,6 +548,7 @@ static int rules_init(rules *R, const orc_params *Q)
     if (Q->n_angular < 2) return ORC_EINVAL;
     if (Q->angular_rule == ORC_ANG_TANH_SINH && Q->n_angular % 2 == 0) return ORC_EINVAL;
     if (Q->angular_rule < ORC_ANG_GL || Q->angular_rule > ORC_ANG_EXACT) return ORC_EINVAL;
+    if (Q->radial_rule != ORC_RAD_MAPPED && Q->radial_rule != ORC_RAD_CLUSTERED) return ORC_EINVAL;
     if (Q->n_radial < 4 || Q->n_radial % 4) return ORC_EINVAL;
     if (!(Q->radial_scale > 0.0) || !(Q->detour_radius > 0.0)) return ORC_EINVAL;
     R->dim = Q->dim;
@@ -502,8 +564,12 @@ static int rules_init(rules *R, const orc_params *Q)
     R->psi = malloc(sizeof(double) * R->n_a);
     R->wpsi = malloc(sizeof(double) * R->n_a);
     R->cpsi = malloc(sizeof(double) * R->n_a);
+    R->gt_x = malloc(sizeof(double) * (R->n_r / 2));
+    R->gt_w = malloc(sizeof(double) * (R->n_r / 2));
     orc_gauss_legendre(R->n_r, R->gr_x, R->gr_w);
     orc_gauss_legendre(ns, R->gs_x, R->gs_w);
+    orc_gauss_legendre(R->n_r / 2, R->gt_x, R->gt_w);
+    R->radial_rule = Q->radial_rule;
     R->exact = Q->angular_rule == ORC_ANG_EXACT;
     int rc = orc_angular_rule(R->exact ? ORC_ANG_GL : Q->angular_rule, R->n_a, R->dim, R->cpsi,
                               R->wpsi);
@@ -596,6 +662,19 @@ int orc_eval_points(const orc_prop *P, const orc_params *Q, const double *x, lon
     if (!(R.r_detour < 0.5 * pole_abs)) {
         rules_free(&R);
         return ORC_EINVAL;
+    }
+    /* the propagator's poles, for the clustered radial rule */
+    if (P->kind == ORC_PROP_SCALAR) {
+        R.ppoles[0] = -P->m2;
+        R.nppoles = 1;
+    } else if (P->kind == ORC_PROP_CPAIR) {
+        R.ppoles[0] = -(P->mk2_re + I * P->mk2_im);
+        R.ppoles[1] = -(P->mq2_re + I * P->mq2_im);
+        R.nppoles = 2;
+    } else if (4.0 * P->c - P->b * P->b > 0.0) {
+        R.ppoles[0] = 0.5 * (-P->b + I * sqrt(4.0 * P->c - P->b * P->b));
+        R.ppoles[1] = conj(R.ppoles[0]);
+        R.nppoles = 2;
     }
 
     /* G0(mu2) on the real axis with the same rules */

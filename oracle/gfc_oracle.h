@@ -15,6 +15,9 @@ enum { ORC_PROP_SCALAR = 0, ORC_PROP_CPAIR = 1, ORC_PROP_DRESSED = 2 };
  * z = cos psi (the paper's), Gauss-Chebyshev of the first and second kind */
 enum { ORC_ANG_GL = 0, ORC_ANG_TANH_SINH = 1, ORC_ANG_CHEB1 = 2, ORC_ANG_CHEB2 = 3,
        ORC_ANG_EXACT = 4 /* the psi integral in closed form (no angular nodes) */ };
+/* radial rules of the rays from q = 0: the mapped half-line, or three panels
+ * sinh-clustered at the propagator pole nearest the ray */
+enum { ORC_RAD_MAPPED = 0, ORC_RAD_CLUSTERED = 1 };
 
 typedef struct {
     int kind;
@@ -32,6 +35,7 @@ typedef struct {
     double radial_scale;        /* L in |q| = L t/(1-t)                       */
     double detour_radius;       /* r of the half circle around a swept pole   */
     int angular_rule;           /* ORC_ANG_*                                  */
+    int radial_rule;            /* ORC_RAD_*                                  */
 } orc_params;
 
 int orc_gauss_legendre(int n, double *x, double *w);

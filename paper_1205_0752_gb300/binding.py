@@ -18,6 +18,7 @@ GFC_PROP_SCALAR, GFC_PROP_CPAIR, GFC_PROP_DRESSED = 0, 1, 2
 GFC_FP64, GFC_MIXED, GFC_F32X2 = 0, 1, 2
 _PRECISION = {"fp64": GFC_FP64, "mixed": GFC_MIXED, "f32x2": GFC_F32X2}
 ANGULAR_RULES = {"gl": 0, "tanh-sinh": 1, "chebyshev1": 2, "chebyshev2": 3, "exact": 4}
+RADIAL_RULES = {"mapped": 0, "clustered": 1}
 
 
 class GfcError(RuntimeError):
@@ -39,7 +40,8 @@ class _Params(ctypes.Structure):
                 ("radial_scale", ctypes.c_double), ("detour_radius", ctypes.c_double),
                 ("precision", ctypes.c_int), ("cut_band", ctypes.c_double),
                 ("pinch_angle", ctypes.c_double), ("mixed_rtol", ctypes.c_double),
-                ("mixed_fallback", ctypes.c_int), ("angular_rule", ctypes.c_int)]
+                ("mixed_fallback", ctypes.c_int), ("angular_rule", ctypes.c_int),
+                ("radial_rule", ctypes.c_int)]
 
 
 class _Grid(ctypes.Structure):
@@ -157,7 +159,8 @@ def make_prop(spec) -> _Prop:
 def make_params(spec=None, **kw) -> _Params:
     """Defaults of gfc_params_default, overridden by ``spec``/keywords;
     ``precision`` and ``mixed_fallback`` may be 'fp64', 'mixed' or 'f32x2',
-    ``angular_rule`` 'gl', 'tanh-sinh', 'chebyshev1', 'chebyshev2' or 'exact'."""
+    ``angular_rule`` 'gl', 'tanh-sinh', 'chebyshev1', 'chebyshev2' or 'exact',
+    ``radial_rule`` 'mapped' or 'clustered'."""
     if isinstance(spec, _Params) and not kw:
         return spec
     lib = load_library()
@@ -170,6 +173,8 @@ def make_params(spec=None, **kw) -> _Params:
             v = _PRECISION.get(v, v)
         if k == "angular_rule":
             v = ANGULAR_RULES.get(v, v)
+        if k == "radial_rule":
+            v = RADIAL_RULES.get(v, v)
         if not hasattr(q, k):
             raise ValueError(f"unknown parameter {k!r}")
         setattr(q, k, type(getattr(q, k))(v))

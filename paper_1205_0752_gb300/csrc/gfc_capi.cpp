@@ -101,6 +101,9 @@ struct Tables {
     double2 *rad64 = nullptr, *seg64 = nullptr, *arc64 = nullptr;
     float2 *rad32 = nullptr, *seg32 = nullptr, *arc32 = nullptr;
     float4 *rad_df = nullptr, *seg_df = nullptr, *arc_df = nullptr;
+    double2 *tail64 = nullptr;
+    float2 *tail32 = nullptr;
+    float4 *tail_df = nullptr;
     double *ang64 = nullptr;
     float *ang32 = nullptr;
     float2 *ang_df = nullptr;
@@ -311,6 +314,9 @@ static int free_tables(Tables &T)
     cudaFree(T.rules64);
     cudaFree(T.rules32);
     cudaFree(T.rad_df);
+    cudaFree(T.tail64);
+    cudaFree(T.tail32);
+    cudaFree(T.tail_df);
     cudaFree(T.seg_df);
     cudaFree(T.arc_df);
     cudaFree(T.ang_df);
@@ -386,6 +392,16 @@ static int build_tables(Tables &T)
         rad64[k] = make_double2(rho, W);
         rad32[k] = make_float2((float)rho, (float)W);
     }
+    // the clustered rule's tail: n_r/2 GL nodes on the same mapped half-line
+    gauss_legendre(T.n_r / 2, gx, gw);
+    std::vector<double2> tail64(T.n_r / 2);
+    std::vector<float2> tail32(T.n_r / 2);
+    for (int k = 0; k < T.n_r / 2; ++k) {
+        double t = 0.5 * (gx[k] + 1.0), omt = 0.5 * (1.0 - gx[k]);
+        double rho = T.L * t / omt, W = T.L / (omt * omt) * 0.5 * gw[k];
+        tail64[k] = make_double2(rho, W);
+        tail32[k] = make_float2((float)rho, (float)W);
+    }
     // detour segments: n_r/4 GL nodes on [0, 1], and cos/sin(pi t) for arcs
     int ns = T.n_r / 4;
     gauss_legendre(ns, gx, gw);
@@ -445,8 +461,9 @@ static int build_tables(Tables &T)
         df u(a), v(b);
         return make_float4(u.hi, u.lo, v.hi, v.lo);
     };
-    std::vector<float4> radD(T.n_r), segD(ns), arcD(ns);
+    std::vector<float4> radD(T.n_r), segD(ns), arcD(ns), tailD(T.n_r / 2);
     for (int k = 0; k < T.n_r; ++k) radD[k] = df4(rad64[k].x, rad64[k].y);
+    for (int k = 0; k < T.n_r / 2; ++k) tailD[k] = df4(tail64[k].x, tail64[k].y);
     for (int k = 0; k < ns; ++k) {
         segD[k] = df4(seg64[k].x, seg64[k].y);
         arcD[k] = df4(arc64[k].x, arc64[k].y);
@@ -462,7 +479,8 @@ static int build_tables(Tables &T)
         (st = upload(&T.rules64, r64, T.bytes)) || (st = upload(&T.rules32, r32, T.bytes)) ||
         (st = upload(&T.rad_df, radD, T.bytes)) || (st = upload(&T.seg_df, segD, T.bytes)) ||
         (st = upload(&T.arc_df, arcD, T.bytes)) || (st = upload(&T.ang_df, angD, T.bytes)) ||
-        (st = upload(&T.rules_df, rulesD, T.bytes)))
+        (st = upload(&T.rules_df, rulesD, T.bytes)) || (st = upload(&T.tail64, tail64, T.bytes)) ||
+        (st = upload(&T.tail32, tail32, T.bytes)) || (st = upload(&T.tail_df, tailD, T.bytes)))
         return st;
     return GFC_OK;
 }
@@ -542,6 +560,8 @@ static int check_params(const gfc_params *p)
         return fail(GFC_EINVAL, "n_angular must be in [2, 512]");
     if (p->angular_rule < GFC_ANG_GAUSS_LEGENDRE || p->angular_rule > GFC_ANG_EXACT)
         return fail(GFC_EINVAL, "angular_rule must be a gfc_angular_rule");
+    if (p->radial_rule != GFC_RAD_MAPPED && p->radial_rule != GFC_RAD_CLUSTERED)
+        return fail(GFC_EINVAL, "radial_rule must be a gfc_radial_rule");
     if (p->angular_rule == GFC_ANG_TANH_SINH && (p->n_angular % 2 == 0 || p->n_angular < 3))
         return fail(GFC_EINVAL, "the tanh-sinh rule needs an odd n_angular >= 3");
     if (!(p->radial_scale > 0.0) || !std::isfinite(p->radial_scale))
@@ -625,6 +645,10 @@ static void fill_kparams_tables(KParams &kp, const gfc_params *p, const Tables &
     kp.arc64 = T.arc64;
     kp.arc32 = T.arc32;
     kp.rad_df = T.rad_df;
+    kp.tail64 = T.tail64;
+    kp.tail32 = T.tail32;
+    kp.tail_df = T.tail_df;
+    kp.radial_rule = p->radial_rule;
     kp.seg_df = T.seg_df;
     kp.arc_df = T.arc_df;
     kp.rules_df = T.rules_df;
@@ -826,6 +850,7 @@ int gfc_params_default(gfc_params *p)
     p->mixed_rtol = 1e-6;
     p->mixed_fallback = GFC_F32X2;
     p->angular_rule = GFC_ANG_GAUSS_LEGENDRE;
+    p->radial_rule = GFC_RAD_MAPPED;
     return GFC_OK;
 }
 

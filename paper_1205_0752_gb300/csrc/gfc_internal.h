@@ -71,6 +71,10 @@ struct KParams {
     const float2 *arc32;
     // double-float copies: (a.hi, a.lo, b.hi, b.lo) per node
     const float4 *rad_df, *seg_df, *arc_df;
+    const double2 *tail64;  // n_r/2 nodes (rho, W) of the mapped half-line
+    const float2 *tail32;   // (the clustered rule's last panel)
+    const float4 *tail_df;
+    int radial_rule;        // gfc_radial_rule
     double L, r_detour, K_D, mu2;
     double Omega, Omega1, delta;     // sum w, sum w t, 4 Omega1 - Omega (pairs)
     PropConst pc;
@@ -135,6 +139,8 @@ struct BatchLaunch {
     int mode;
     int npair;
     int rules_total;             // compressed-rule nodes of the launch's angular rule
+    int radial_rule;             // gfc_radial_rule shared by the launch's requests
+    int ang_exact;               // closed-form angle, shared likewise
 };
 
 cudaError_t launch_batch(const BatchLaunch &bl, const DevTables &tb, int arith, bool two_terms,

@@ -26,7 +26,7 @@ g0mu_kernel(const __grid_constant__ KParams kp,
     const int lane = threadIdx.x & 31;
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
-    Plan<double> P = make_plan<double>(kp, mu2, 0.0);
+    Plan<double> P = make_plan<double, 1>(kp, mu2, 0.0);
     C<double> x = {mu2, 0.0};
     C<double> e2 = P.eth * P.eth;
     C<double> eD = kp.dim == 4 ? e2 * e2 : e2 * P.eth;
@@ -36,13 +36,14 @@ g0mu_kernel(const __grid_constant__ KParams kp,
     const PassPre<double, 2> pp2 = pass_pre<double, 2>(kp, P, 0, x);
     const PassPre<double, 1> pp1 = pass_pre<double, 1>(kp, P, 0, x);
     for (int k = warp * 32 + lane; k < nn; k += nwarps * 32) {
-        Node<double> nd = ray_node<double>(kp, k, P.eth, eD, 0.0);
+        Node<double> nd = P.clus ? ray_node_cl<double>(kp, k, P.eth, eD, P.cl_c, P.cl_d, P.cl_eta)
+                                 : ray_node<double>(kp, k, P.eth, eD, 0.0);
         ErrAcc<double> ea = {0.0, 0.0};
         double qm;
         int np;
         C<double> v = P.nterm[0] == 2
-                          ? node_value<double, NP, 2>(kp, tab, stab, srules, pp2, x, nd, ea, qm, np)
-                          : node_value<double, NP, 1>(kp, tab, stab, srules, pp1, x, nd, ea, qm, np);
+                          ? node_value<double, NP, 2, 1>(kp, tab, stab, srules, pp2, x, nd, ea, qm, np)
+                          : node_value<double, NP, 1, 1>(kp, tab, stab, srules, pp1, x, nd, ea, qm, np);
         sr += v.r;
         si += v.i;
     }
@@ -93,6 +94,8 @@ __global__ void grid_points_kernel(double re0, double dre, double im0, double di
 template <typename T>
 static cudaError_t eval_np(const KParams &kp, const DevTables &tb, cudaStream_t st)
 {
+    // the closed-form angle and the clustered radial rule: generic variant kernels
+    if (kp.radial_rule == 1 || kp.ang_exact) return eval_inst<T, 0>(kp, tb, st);
     if constexpr (std::is_same<T, df>::value) {
         return eval_inst<T, 0>(kp, tb, st);
     } else {
@@ -109,6 +112,7 @@ template <typename T>
 static cudaError_t batch_np(const BatchLaunch &bl, const DevTables &tb, bool two_terms,
                             cudaStream_t st)
 {
+    if (bl.radial_rule == 1 || bl.ang_exact) return batch_inst<T, 0>(bl, tb, two_terms, st);
     if constexpr (std::is_same<T, df>::value) {
         return batch_inst<T, 0>(bl, tb, two_terms, st);
     } else {

@@ -134,6 +134,8 @@ struct Plan {
     Term<T> term[2][2];
     C<T> eth;    // e^{i arg(x)/2}: direction of the q-ray
     C<T> yp;     // pole passed by the detour
+    int clus;    // clustered radial rule on the ray of pass 0
+    double cl_c, cl_d, cl_eta;   // its centre c, width d and asinh(c/d)
 };
 
 template <typename T>
@@ -151,19 +153,18 @@ __device__ __forceinline__ double ray_distance(double y0r, double y0i, double ph
 
 // The plan is decided in binary64 (it selects among contours), then its
 // numbers are rounded to T.
-template <typename T>
-__device__ Plan<T> make_plan(const KParams &kp, double xr, double xi)
+template <typename T, int CL = 0>
+__device__ __forceinline__ Plan<T> make_plan(const KParams &kp, double xr, double xi)
 {
     Plan<T> P;
     const PropConst &pc = kp.pc;
     double phi = atan2(xi, xr);
     double ax = sqrt(xr * xr + xi * xi);
     // e^{i phi/2} as the principal root of x/|x|
-    {
-        C<double> u = ax > 0.0 ? C<double>{xr / ax, xi / ax} : C<double>{1.0, 0.0};
-        C<double> e = csqrt_p(u);
-        P.eth = cvt<T>(e.r, e.i);
-    }
+    const C<double> eth = csqrt_p(ax > 0.0 ? C<double>{xr / ax, xi / ax} : C<double>{1.0, 0.0});
+    P.eth = cvt<T>(eth.r, eth.i);
+    P.clus = 0;
+    P.cl_c = P.cl_d = P.cl_eta = 0.0;
     P.npass = 1;
     P.kind[0] = PASS_RAY;
     P.kind[1] = PASS_RAY;
@@ -224,6 +225,33 @@ __device__ Plan<T> make_plan(const KParams &kp, double xr, double xi)
             P.yp = cvt<T>(yk.r, yk.i);
         }
     }
+    if (CL && kp.radial_rule == 1 && P.kind[0] == PASS_RAY) {
+        // clustered radial rule: of the q-plane points +-sqrt(y_p) of the
+        // propagator's poles, the one closest in angle to the ray, with
+        // distance d < 0.75 of its projection c on the ray
+        C<double> ys[2];
+        int ny = 2;
+        if (pc.kind == 0) { ys[0] = {-pc.m2, 0.0}; ny = 1; }
+        else if (pc.kind == 1) { ys[0] = {pc.yu_re, pc.yu_im}; ys[1] = {pc.yu_re, -pc.yu_im}; }
+        else { ys[0] = {pc.yp_re, pc.yp_im}; ys[1] = {pc.yp_re, -pc.yp_im}; }
+        double best = 1.0;
+        for (int i = 0; i < ny; ++i) {
+            const C<double> z = csqrt_p(ys[i]) * conj(eth);
+            for (int sg = -1; sg <= 1; sg += 2) {
+                const double rs = sg * z.r, ds = fabs(z.i);
+                if (rs > 0.0 && ds < 0.75 * rs && ds / rs < best) {
+                    best = ds / rs;
+                    P.clus = 1;
+                    P.cl_c = rs;
+                    P.cl_d = ds;
+                }
+            }
+        }
+        if (P.clus) {
+            P.cl_d = fmax(P.cl_d, 1e-12 * P.cl_c);
+            P.cl_eta = asinh(P.cl_c / P.cl_d);
+        }
+    }
     return P;
 }
 
@@ -259,7 +287,7 @@ template <>
 __device__ __forceinline__ void load2<double>(const KParams &kp, int which, int k, double &a,
                                               double &b)
 {
-    const double2 *p = which == 0 ? kp.rad64 : (which == 1 ? kp.seg64 : kp.arc64);
+    const double2 *p = which == 0 ? kp.rad64 : (which == 1 ? kp.seg64 : (which == 2 ? kp.arc64 : kp.tail64));
     double2 v = __ldg(p + k);
     a = v.x;
     b = v.y;
@@ -268,7 +296,7 @@ __device__ __forceinline__ void load2<double>(const KParams &kp, int which, int 
 template <>
 __device__ __forceinline__ void load2<df>(const KParams &kp, int which, int k, df &a, df &b)
 {
-    const float4 *p = which == 0 ? kp.rad_df : (which == 1 ? kp.seg_df : kp.arc_df);
+    const float4 *p = which == 0 ? kp.rad_df : (which == 1 ? kp.seg_df : (which == 2 ? kp.arc_df : kp.tail_df));
     float4 v = __ldg(p + k);
     a = df(v.x, v.y);
     b = df(v.z, v.w);
@@ -278,19 +306,17 @@ template <>
 __device__ __forceinline__ void load2<float>(const KParams &kp, int which, int k, float &a,
                                              float &b)
 {
-    const float2 *p = which == 0 ? kp.rad32 : (which == 1 ? kp.seg32 : kp.arc32);
+    const float2 *p = which == 0 ? kp.rad32 : (which == 1 ? kp.seg32 : (which == 2 ? kp.arc32 : kp.tail32));
     float2 v = __ldg(p + k);
     a = v.x;
     b = v.y;
 }
 
-// q-ray node: q = (rho0 + rho_k) e^{i theta}, measure q^(D-1) dq
+// q-ray node at |q| = rho with weight W: q = rho e^{i theta}, measure
+// q^(D-1) dq
 template <typename T>
-__device__ __forceinline__ Node<T> ray_node(const KParams &kp, int k, C<T> eth, C<T> eD, T rho0)
+__device__ __forceinline__ Node<T> ray_node_at(const KParams &kp, T rho, T W, C<T> eth, C<T> eD)
 {
-    T rho, W;
-    load2<T>(kp, 0, k, rho, W);
-    rho += rho0;
     Node<T> n;
     C<T> q = rho * eth;
     n.y = q * q;
@@ -304,6 +330,72 @@ __device__ __forceinline__ Node<T> ray_node(const KParams &kp, int k, C<T> eth, 
     T mag = (kp.dim == 4 ? rs * rho : rs) * W;
     n.Jt = mag * eD;
     return n;
+}
+
+// node k of the mapped ray from |q| = rho0
+template <typename T>
+__device__ __forceinline__ Node<T> ray_node(const KParams &kp, int k, C<T> eth, C<T> eD, T rho0)
+{
+    T rho, W;
+    load2<T>(kp, 0, k, rho, W);
+    return ray_node_at<T>(kp, rho + rho0, W, eth, eD);
+}
+
+// node k of the clustered ray: n_s nodes on [0, c] and on [c, 2c] with
+// |q| = c + d sinh(s), s = eta (t - 1) or eta t, dq = d cosh(s) eta dt, then
+// the n_r/2 tail nodes from 2c
+__device__ __forceinline__ void cl_rho_w(const KParams &kp, int k, double c, double d,
+                                         double eta, double &rho, double &W)
+{
+    const int ns = kp.n_s;
+    if (k < 2 * ns) {
+        double t, w;
+        load2<double>(kp, 1, k < ns ? k : k - ns, t, w);
+        const double sv = k < ns ? eta * (t - 1.0) : eta * t;
+        const double e = exp(sv), ie = rcp(e);
+        rho = c + d * (0.5 * (e - ie));
+        W = d * (0.5 * (e + ie)) * eta * w;
+    } else {
+        double rt, wt;
+        load2<double>(kp, 3, k - 2 * ns, rt, wt);
+        rho = 2.0 * c + rt;
+        W = wt;
+    }
+}
+__device__ __forceinline__ void cl_rho_w(const KParams &kp, int k, double c, double d,
+                                         double eta, float &rho, float &W)
+{
+    const int ns = kp.n_s;
+    if (k < 2 * ns) {
+        float t, w;
+        load2<float>(kp, 1, k < ns ? k : k - ns, t, w);
+        const float sv = k < ns ? (float)eta * (t - 1.0f) : (float)eta * t;
+        const float e = expf(sv), ie = rcp(e);
+        rho = (float)c + (float)d * (0.5f * (e - ie));
+        W = (float)d * (0.5f * (e + ie)) * (float)eta * w;
+    } else {
+        float rt, wt;
+        load2<float>(kp, 3, k - 2 * ns, rt, wt);
+        rho = 2.0f * (float)c + rt;
+        W = wt;
+    }
+}
+__device__ __forceinline__ void cl_rho_w(const KParams &kp, int k, double c, double d,
+                                         double eta, df &rho, df &W)
+{
+    double r, w;
+    cl_rho_w(kp, k, c, d, eta, r, w);
+    rho = df(r);
+    W = df(w);
+}
+
+template <typename T>
+__device__ __forceinline__ Node<T> ray_node_cl(const KParams &kp, int k, C<T> eth, C<T> eD,
+                                               double c, double d, double eta)
+{
+    T rho, W;
+    cl_rho_w(kp, k, c, d, eta, rho, W);
+    return ray_node_at<T>(kp, rho, W, eth, eD);
 }
 
 template <typename T>
@@ -674,7 +766,7 @@ __device__ __forceinline__ df trsqrt(df x) { return df(rsqrtf(x.hi), 0.0f); }
 // inputs: |y|/|y + M2| per propagator factor (the contour passes near a pole
 // when arg x is near pi), (|x| + |y|)/|a| for the denominator a, and
 // |w|/|1 - w t|_min for the angular sum next to a pinch (binary32 only).
-template <typename T, int NP, int NT>
+template <typename T, int NP, int NT, int V>
 __device__ __forceinline__ C<T> node_value(const KParams &kp, const AngTab<T, tab_size<NP>()> &tab,
                                            const T *stab, const void *srules,
                                            const PassPre<T, NT> &pp, C<T> x, const Node<T> &nd,
@@ -695,7 +787,7 @@ __device__ __forceinline__ C<T> node_value(const KParams &kp, const AngTab<T, ta
     }
     T A[NT], B[NT];
     C<T> Sx[NT];
-    if (kp.ang_exact) {
+    if (V && kp.ang_exact) {
         qmin = T(1e30);
 #pragma unroll
         for (int s = 0; s < NT; ++s) {
@@ -714,7 +806,7 @@ __device__ __forceinline__ C<T> node_value(const KParams &kp, const AngTab<T, ta
     for (int s = 0; s < NT; ++s) {
         if (s >= pp.nt) break;
         C<T> S;
-        if (kp.ang_exact) {
+        if (V && kp.ang_exact) {
             S = Sx[s];
         } else {
             C<T> T2 = {A[s] - w[s].r * B[s], w[s].i * B[s]};
@@ -826,8 +918,11 @@ __device__ __forceinline__ void point_x(const KParams &kp, int64_t p, double &xr
     }
 }
 
-// One pass of a point's contour, the lane's share of its nodes.
-template <typename T, int NP, int NTT>
+// One pass of a point's contour, the lane's share of its nodes. CL = 1 (the
+// variant kernels) compiles in the options that the default kernels leave
+// out so as to carry none of their registers: the closed-form angular
+// integral and the clustered radial rule.
+template <typename T, int NP, int NTT, int CL>
 __device__ __forceinline__ void run_pass(const KParams &kp, const AngTab<T, tab_size<NP>()> &tab,
                                          const T *stab, const void *srules, const Plan<T> &P,
                                          int pass, C<T> x, C<T> eD, int lane, Acc<T> &acc,
@@ -837,11 +932,12 @@ __device__ __forceinline__ void run_pass(const KParams &kp, const AngTab<T, tab_
     const bool ray = P.kind[pass] == PASS_RAY;
     const int nn = ray ? kp.n_r : 3 * kp.n_s + kp.n_r;
     for (int k = lane; k < nn; k += 32) {
-        Node<T> nd = ray ? ray_node<T>(kp, k, P.eth, eD, T(0))
-                         : detour_node<T>(kp, k, P.eth, eD, P.yp, x);
+        Node<T> nd = !ray ? detour_node<T>(kp, k, P.eth, eD, P.yp, x)
+                          : ((CL && P.clus) ? ray_node_cl<T>(kp, k, P.eth, eD, P.cl_c, P.cl_d, P.cl_eta)
+                                            : ray_node<T>(kp, k, P.eth, eD, T(0)));
         T qm;
         int np;
-        C<T> v = node_value<T, NP, NTT>(kp, tab, stab, srules, pp, x, nd, ea, qm, np);
+        C<T> v = node_value<T, NP, NTT, CL>(kp, tab, stab, srules, pp, x, nd, ea, qm, np);
         acc_add(acc, v);
         qall = fmin(qall, qm);
         pairs += np;
@@ -850,13 +946,13 @@ __device__ __forceinline__ void run_pass(const KParams &kp, const AngTab<T, tab_
 
 // Sum over one point's contour, per lane, into acc; returns the point's
 // number of contour nodes.
-template <typename T, int NP, int NT>
+template <typename T, int NP, int NT, int CL>
 __device__ __forceinline__ int point_sum(const KParams &kp, const AngTab<T, tab_size<NP>()> &tab,
                                          const T *stab, const void *srules, double xr, double xi,
                                          int lane, Acc<T> &acc, ErrAcc<T> &ea, T &qall,
                                          int &pairs)
 {
-    const Plan<T> P = make_plan<T>(kp, xr, xi);
+    const Plan<T> P = make_plan<T, CL>(kp, xr, xi);
     const C<T> x = cvt<T>(xr, xi);
     // e^{i D theta} of the ray, once per point
     const C<T> e2 = P.eth * P.eth;
@@ -867,10 +963,11 @@ __device__ __forceinline__ int point_sum(const KParams &kp, const AngTab<T, tab_
         if (pass >= P.npass) break;
         total += P.kind[pass] == PASS_RAY ? kp.n_r : 3 * kp.n_s + kp.n_r;
         if (NT > 1 && P.nterm[pass] == 2)
-            run_pass<T, NP, (NT > 1 ? 2 : 1)>(kp, tab, stab, srules, P, pass, x, eD, lane, acc,
-                                             ea, qall, pairs);
+            run_pass<T, NP, (NT > 1 ? 2 : 1), CL>(kp, tab, stab, srules, P, pass, x, eD, lane,
+                                                 acc, ea, qall, pairs);
         else
-            run_pass<T, NP, 1>(kp, tab, stab, srules, P, pass, x, eD, lane, acc, ea, qall, pairs);
+            run_pass<T, NP, 1, CL>(kp, tab, stab, srules, P, pass, x, eD, lane, acc, ea, qall,
+                                   pairs);
     }
     return total;
 }
@@ -883,7 +980,7 @@ __device__ __forceinline__ void list_append(const KParams &kp, int64_t p)
 
 // Evaluates point p of the request described by kp under `mode`; the whole
 // warp calls it with the same p.
-template <typename T, int NP, int NT>
+template <typename T, int NP, int NT, int CL>
 __device__ __forceinline__ void eval_point(const KParams &kp, const AngTab<T, tab_size<NP>()> &tab,
                                            const T *stab, const void *srules, int64_t p, int mode,
                                            int lane)
@@ -911,7 +1008,7 @@ __device__ __forceinline__ void eval_point(const KParams &kp, const AngTab<T, ta
     ErrAcc<T> ea = {T(0), T(0)};
     T qall = T(1e30);
     int pairs = 0;
-    int nodes = point_sum<T, NP, NT>(kp, tab, stab, srules, xr, xi, lane, acc, ea, qall, pairs);
+    int nodes = point_sum<T, NP, NT, CL>(kp, tab, stab, srules, xr, xi, lane, acc, ea, qall, pairs);
     if (kp.node_count && lane == 0)
         atomicAdd(kp.node_count, (unsigned long long)nodes * (unsigned long long)(2 * kp.npair));
     if (kp.pair_count) {
@@ -986,7 +1083,7 @@ __device__ __forceinline__ void stage_tables(const KParams &kp, const T *gtab, i
 }
 
 // One request: warps take points from an atomic counter until none is left.
-template <typename T, int NP, int NT>
+template <typename T, int NP, int NT, int CL>
 __global__ void __launch_bounds__(256)
 eval_kernel(const __grid_constant__ KParams kp,
             const __grid_constant__ AngTab<T, tab_size<NP>()> tab, const T *__restrict__ gtab)
@@ -1003,7 +1100,7 @@ eval_kernel(const __grid_constant__ KParams kp,
         p = __shfl_sync(0xffffffffu, p, 0);
         if (p >= n) break;
         int64_t pt = kp.mode == MODE_LIST64 ? kp.list[p] : (int64_t)p;
-        eval_point<T, NP, NT>(kp, tab, stab, srules, pt, kp.mode, lane);
+        eval_point<T, NP, NT, CL>(kp, tab, stab, srules, pt, kp.mode, lane);
     }
 }
 
@@ -1011,7 +1108,7 @@ eval_kernel(const __grid_constant__ KParams kp,
 // points [items[i].p0, items[i].p1) of request slot items[i].slot; offs[i] is
 // its first index in the launch-wide point count. All requests of a launch
 // share the angular rule (n_angular, D) held in the constant bank.
-template <typename T, int NP, int NT>
+template <typename T, int NP, int NT, int CL>
 __global__ void __launch_bounds__(256)
 eval_batch_kernel(const KParams *__restrict__ slots, const BatchItem *__restrict__ items,
                   const int64_t *__restrict__ offs, int nitems, int64_t total,
@@ -1037,8 +1134,8 @@ eval_batch_kernel(const KParams *__restrict__ slots, const BatchItem *__restrict
         const BatchItem it = items[lo];
         const KParams &kp = slots[it.slot];
         int64_t q = it.p0 + ((int64_t)p - offs[lo]);
-        eval_point<T, NP, NT>(kp, tab, stab, srules, mode == MODE_LIST64 ? kp.list[q] : q, mode,
-                              lane);
+        eval_point<T, NP, NT, CL>(kp, tab, stab, srules, mode == MODE_LIST64 ? kp.list[q] : q,
+                                  mode, lane);
     }
 }
 
@@ -1076,7 +1173,7 @@ inline const float *gtab_of<float>(const DevTables &tb) { return tb.ang32; }
 template <>
 inline const df *gtab_of<df>(const DevTables &tb) { return reinterpret_cast<const df *>(tb.ang_df); }
 
-template <typename T, int NP, int NT>
+template <typename T, int NP, int NT, int CL>
 static cudaError_t run_eval(const KParams &kp, const DevTables &tb, cudaStream_t st)
 {
     AngTab<T, tab_size<NP>()> tab;
@@ -1084,18 +1181,18 @@ static cudaError_t run_eval(const KParams &kp, const DevTables &tb, cudaStream_t
     size_t smem = smem_bytes<T, NP>(kp.npair, kp.rules_total);
     int blocks_per_sm = 0;
     cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        &blocks_per_sm, (const void *)eval_kernel<T, NP, NT>, 256, smem);
+        &blocks_per_sm, (const void *)eval_kernel<T, NP, NT, CL>, 256, smem);
     if (err != cudaSuccess) return err;
     if (blocks_per_sm < 1) blocks_per_sm = 1;
     int64_t blocks = (kp.npts + 7) / 8;
     int64_t cap = (int64_t)sm_count() * blocks_per_sm;
     if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
-    eval_kernel<T, NP, NT><<<(unsigned)blocks, 256, smem, st>>>(kp, tab, gtab_of<T>(tb));
+    eval_kernel<T, NP, NT, CL><<<(unsigned)blocks, 256, smem, st>>>(kp, tab, gtab_of<T>(tb));
     return cudaGetLastError();
 }
 
-template <typename T, int NP, int NT>
+template <typename T, int NP, int NT, int CL>
 static cudaError_t run_batch(const BatchLaunch &bl, const DevTables &tb, cudaStream_t st)
 {
     AngTab<T, tab_size<NP>()> tab;
@@ -1103,14 +1200,14 @@ static cudaError_t run_batch(const BatchLaunch &bl, const DevTables &tb, cudaStr
     size_t smem = smem_bytes<T, NP>(bl.npair, bl.rules_total);
     int blocks_per_sm = 0;
     cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        &blocks_per_sm, (const void *)eval_batch_kernel<T, NP, NT>, 256, smem);
+        &blocks_per_sm, (const void *)eval_batch_kernel<T, NP, NT, CL>, 256, smem);
     if (err != cudaSuccess) return err;
     if (blocks_per_sm < 1) blocks_per_sm = 1;
     int64_t blocks = (bl.total + 7) / 8;
     int64_t cap = (int64_t)sm_count() * blocks_per_sm;
     if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
-    eval_batch_kernel<T, NP, NT><<<(unsigned)blocks, 256, smem, st>>>(
+    eval_batch_kernel<T, NP, NT, CL><<<(unsigned)blocks, 256, smem, st>>>(
         bl.slots, bl.items, bl.offs, bl.nitems, bl.total, bl.counter, bl.mode, tab,
         gtab_of<T>(tb), bl.npair);
     return cudaGetLastError();

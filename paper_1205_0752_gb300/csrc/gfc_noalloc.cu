@@ -110,9 +110,10 @@ extern "C" int gfc_eval_points_noalloc(const gfc_propagator *prop, const gfc_par
         return fail(GFC_EINVAL, "gfc_eval_points_noalloc evaluates in GFC_FP64 only");
     if (params->n_radial > kNaMaxRadial || params->n_angular > kNaMaxAngular)
         return fail(GFC_EINVAL, "gfc_eval_points_noalloc: n_radial <= 4096 and n_angular <= 512");
-    if (params->n_angular % 2 || params->angular_rule != GFC_ANG_GAUSS_LEGENDRE)
-        return fail(GFC_EINVAL,
-                    "gfc_eval_points_noalloc: even n_angular with the Gauss-Legendre rule only");
+    if (params->n_angular % 2 || params->angular_rule != GFC_ANG_GAUSS_LEGENDRE ||
+        params->radial_rule != GFC_RAD_MAPPED)
+        return fail(GFC_EINVAL, "gfc_eval_points_noalloc: even n_angular, the Gauss-Legendre "
+                                "angular and the mapped radial rule only");
     if (npts < 0) return fail(GFC_EINVAL, "npts < 0");
     if (npts > 0 && (!x || !G)) return fail(GFC_EINVAL, "x and G must be device pointers");
     if (((uintptr_t)x | (uintptr_t)G) & 15) return fail(GFC_EINVAL, "x and G must be 16-byte aligned");

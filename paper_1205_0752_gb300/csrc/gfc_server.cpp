@@ -94,9 +94,9 @@ struct LaunchRec {
     int64_t *offs_host = nullptr;       // pinned
 };
 
-// arith, npair, dim, two terms, mode, angular rule: the requests of one launch
-// share its angular tables
-using GroupKey = std::tuple<int, int, int, int, int, int>;
+// arith, npair, dim, two terms, mode, angular rule, radial rule: the requests
+// of one launch share its angular tables and its kernel
+using GroupKey = std::tuple<int, int, int, int, int, int, int>;
 
 }  // namespace
 
@@ -294,7 +294,8 @@ void issue_launches(gfc_server *s)
             const Phase &ph = r->phases[p];
             if (ph.end < 0 || ph.next >= ph.end) continue;
             GroupKey k{ph.arith, npair_of(&r->params), r->params.dim,
-                       r->prop.kind == GFC_PROP_DRESSED ? 1 : 0, ph.mode, r->params.angular_rule};
+                       r->prop.kind == GFC_PROP_DRESSED ? 1 : 0, ph.mode, r->params.angular_rule,
+                       r->params.radial_rule};
             groups[k].push_back({r, p});
         }
     }
@@ -363,6 +364,8 @@ void issue_launches(gfc_server *s)
         bl.npair = std::get<1>(key);
         Request *r0 = members.front().first;
         bl.rules_total = r0->kp.rules_total;
+        bl.radial_rule = std::get<6>(key);
+        bl.ang_exact = std::get<5>(key) == GFC_ANG_EXACT;
         cudaError_t e = launch_batch(bl, dev_tables_c(*r0->T), arith, std::get<3>(key) != 0, st);
         if (e != cudaSuccess) {
             s->error = GFC_ECUDA;

@@ -38,7 +38,7 @@ def assert_parity(G, ref, rtol, x=None, what=""):
 
 def oracle_params(p):
     return {k: p[k] for k in ("dim", "mu2", "n_radial", "n_angular", "radial_scale",
-                              "detour_radius", "angular_rule") if k in p}
+                              "detour_radius", "angular_rule", "radial_rule") if k in p}
 
 
 def run_grid(prop, params, rect, m, n):
@@ -277,3 +277,43 @@ def test_exact_angular_production_sampled():
     x = oracle.grid_points(*rect, 1024, 1024)[idx]
     ref = oracle.eval_points(SCALAR, oracle_params(par), x)
     assert_parity(G[idx], ref, RTOL["fp64"], x, "exact angular production")
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed", "f32x2"])
+@pytest.mark.parametrize("angular", ["exact", "gl"])
+@pytest.mark.parametrize("case", ["bubble", "paper", "dressed3", "dressed4"])
+def test_clustered_radial_rule(case, angular, precision):
+    """The sinh-clustered radial rule (variant kernels) against the oracle's,
+    with the closed-form angle and with the Gauss-Legendre rule."""
+    if case == "bubble":
+        prop, rect, m, n, dim, mu2 = SCALAR, si.grid_rect("small"), 48, 40, 4, 1.0
+    elif case == "paper":
+        prop, rect, m, n, dim, mu2 = PAPER, si.grid_rect("paper"), 48, 40, 4, 0.0
+    else:
+        a, b, c = si.dressed_draws(3, 1)[0]
+        prop = {"kind": "dressed", "a": a, "b": b, "c": c}
+        rect, m, n, dim, mu2 = si.grid_rect("small"), 32, 24, int(case[-1]), 1.0
+    par = dict(dim=dim, mu2=mu2, n_radial=512, n_angular=2 if angular == "exact" else 64,
+               angular_rule=angular, radial_rule="clustered", precision=precision)
+    G = run_grid(prop, par, rect, m, n)
+    x = oracle.grid_points(*rect, m, n)
+    ref = oracle.eval_points(prop, oracle_params(par), x)
+    # double-float carries ~48 bits; the clustered nodes come within d of a
+    # pole, where a node's relative condition |y|/|y + M2| reaches ~1/d, so
+    # its bound is 2^-48/d: 5e-10 here (d >= ~1e-4 on these grids)
+    rtol = 5e-10 if precision == "f32x2" else RTOL[precision]
+    assert_parity(G, ref, rtol, x, f"clustered {case} {angular} {precision}")
+
+
+def test_clustered_near_axis_band():
+    """Points within 0.05 of the negative real axis (beyond and below the
+    threshold -4 m^2), 8192 radial nodes, closed-form angle: the case the
+    clustered rule exists for."""
+    re = np.linspace(-9.9, -0.1, 50)
+    x = np.concatenate([re + 0.01j, re - 0.03j, re + 0.049j])
+    par = dict(dim=4, mu2=1.0, n_radial=8192, n_angular=2, angular_rule="exact",
+               radial_rule="clustered")
+    G = gfc.eval_points(SCALAR, par, torch.tensor(x, device="cuda"))
+    torch.cuda.synchronize()
+    ref = oracle.eval_points(SCALAR, oracle_params(par), x)
+    assert_parity(G.cpu().numpy(), ref, RTOL["fp64"], x, "clustered near-axis band")
