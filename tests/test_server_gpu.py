@@ -17,7 +17,7 @@ if not torch.cuda.is_available():
 
 import paper_1205_0752_gb300 as gfc  # noqa: E402
 
-RTOL = {"fp64": 1e-10, "mixed": 1e-6}
+RTOL = {"fp64": 1e-10, "mixed": 1e-6, "f32x2": 1e-10}
 RECT = si.grid_rect("small")
 
 
@@ -33,6 +33,16 @@ def _mix():
                                                              precision="fp64"), 56),
         ({"kind": "scalar", "m2": 4.0}, dict(dim=4, n_radial=512, n_angular=256, precision="mixed"), 64),
         ({"kind": "scalar", "m2": 1.0}, dict(dim=4, n_radial=256, n_angular=10, precision="fp64"), 34),
+        # other rules: same n_angular and dim as the first request, so only the
+        # rules keep them out of its launches
+        ({"kind": "scalar", "m2": 1.0}, dict(dim=4, n_radial=256, n_angular=64, precision="fp64",
+                                             angular_rule="chebyshev2"), 40),
+        ({"kind": "scalar", "m2": 1.0}, dict(dim=4, n_radial=256, n_angular=49, precision="f32x2",
+                                             angular_rule="tanh-sinh"), 36),
+        ({"kind": "scalar", "m2": 1.0}, dict(dim=4, n_radial=512, n_angular=64, precision="fp64",
+                                             angular_rule="exact", radial_rule="clustered"), 44),
+        (dressed, dict(dim=3, n_radial=512, n_angular=64, precision="mixed",
+                       angular_rule="exact", radial_rule="clustered"), 30),
     ]
 
 
