@@ -230,9 +230,10 @@ static void build_rules(Tables &T, std::vector<double> &r64, std::vector<float4>
         }
         for (int j = 0; j < N; ++j) Q[k + 1][j] = v[j] / b;
     }
-    // thresholds: relative error ~ 10 rho^(-2n) below 2^-58 (binary64) and
-    // 2^-26 (binary32)
-    const double K64 = 0.5 * std::log(10.0 * std::pow(2.0, 58)), K32 = 0.5 * std::log(10.0 * std::pow(2.0, 26));
+    // thresholds: relative error ~ 10 rho^(-2n) below 2^-52 (binary64, the
+    // unit roundoff: even a cancellation of 1e4 in the sums leaves ~2e-12)
+    // and 2^-26 (binary32)
+    const double K64 = 0.5 * std::log(10.0 * std::pow(2.0, 52)), K32 = 0.5 * std::log(10.0 * std::pow(2.0, 26));
     for (int n : ns) {
         if (n > kmax) break;
         std::vector<double> d(alpha.begin(), alpha.begin() + n), sub(beta.begin(), beta.begin() + n - 1), z;
