@@ -671,6 +671,15 @@ static void fill_kparams_tables(KParams &kp, const gfc_params *p, const Tables &
     kp.rules32 = T.rules32;
     kp.rules_total = T.rules_total;
     kp.pc = pc;
+    {
+        const double c[6] = {kp.Omega1, kp.delta, pc.yp_re, pc.yp_im, pc.Rp_re, pc.Rp_im};
+        for (int i = 0; i < 6; ++i) {
+            df v(c[i]);
+            kp.f32c[i] = (float)c[i];
+            kp.dfc[2 * i] = v.hi;
+            kp.dfc[2 * i + 1] = v.lo;
+        }
+    }
     kp.cut_band = p->cut_band;
     kp.pinch_angle = p->pinch_angle;
     kp.mixed_rtol = p->mixed_rtol;

@@ -55,6 +55,10 @@ struct KParams {
     int npair;           // angular pairs ((n_angular + 1) / 2; 0 with ang_exact)
     int mode;            // LaunchMode
     int ang_exact;       // angular integral in closed form (GFC_ANG_EXACT)
+    // Omega1, delta, Re/Im of the dressed pole yp and residue Rp, as binary32
+    // and as double-float (hi, lo) pairs, for the kernels of those arithmetics
+    float f32c[6];
+    float dfc[12];
     int use_grid;        // 1: x from the grid spec, 0: from x[]
     int64_t npts;
     // grid (Kernel 1)

@@ -158,7 +158,8 @@ __device__ __forceinline__ Plan<T> make_plan(const KParams &kp, double xr, doubl
 {
     Plan<T> P;
     const PropConst &pc = kp.pc;
-    double phi = atan2(xi, xr);
+    // arg x decides the contour only for poles off the real axis
+    const double phi = pc.kind == 0 ? 0.0 : atan2(xi, xr);
     double ax = sqrt(xr * xr + xi * xi);
     // e^{i phi/2} as the principal root of x/|x|
     const C<double> eth = csqrt_p(ax > 0.0 ? C<double>{xr / ax, xi / ax} : C<double>{1.0, 0.0});
@@ -263,7 +264,8 @@ __device__ __forceinline__ bool in_band(const KParams &kp, double xr, double xi)
     const PropConst &pc = kp.pc;
     double d = xr <= pc.thr ? fabs(xi) : sqrt((xr - pc.thr) * (xr - pc.thr) + xi * xi);
     if (d < kp.cut_band) return true;
-    if (pc.pinch > 0.0 && fabs(fabs(atan2(xi, xr)) - pc.pinch) < kp.pinch_angle) return true;
+    if (kp.pinch_angle > 0.0 && pc.pinch > 0.0 && fabs(fabs(atan2(xi, xr)) - pc.pinch) < kp.pinch_angle)
+        return true;
     return false;
 }
 
@@ -418,22 +420,53 @@ __device__ __forceinline__ Node<T> finish_y_node(const KParams &kp, C<T> y, C<T>
     return n;
 }
 
+// Per-pass constants of a detour around the pole yp (computed once per point)
+template <typename T>
+struct DetourPre {
+    C<T> yp, u, q1, y0, d;   // pole, yp/|yp|, end of the q-segment, outer segment y0 -> y0 + d
+    T r, sqRd, sgpr, sg;     // radius, sqrt(R_d), sign(Im yp) pi r, sign(Im yp)
+};
+
+template <typename T>
+__device__ __forceinline__ DetourPre<T> detour_pre(const KParams &kp, C<T> eth, C<T> yp, C<T> x)
+{
+    DetourPre<T> dp;
+    const T ap = tsqrt(cabs2(yp));
+    dp.yp = yp;
+    dp.u = rcp(ap) * yp;
+    dp.r = T(kp.r_detour);
+    const T Rd = tsqrt(cabs2(x)) + T(20);
+    dp.sqRd = tsqrt(Rd);
+    dp.q1 = csqrt_p((ap - dp.r) * dp.u);
+    dp.y0 = (ap + dp.r) * dp.u;
+    dp.d = Rd * (eth * eth) - dp.y0;
+    dp.sg = yp.i > T(0) ? T(1) : T(-1);
+    dp.sgpr = dp.sg * T(PI_D()) * dp.r;
+    return dp;
+}
+
+// A warp's DetourPre lives in shared memory (one slot per warp of a block of
+// 256): held in registers across the node loop it raised the register count
+// of every kernel, ray-only ones included.
+template <typename T>
+__device__ __forceinline__ DetourPre<T> *detour_slot()
+{
+    __shared__ DetourPre<T> slots[8];
+    return &slots[threadIdx.x >> 5];
+}
+
 // detour node k of 3 n_s + n_r: q-segment 0 -> q1, half circle around yp,
 // straight segment out to R_d e^{i phi}, ray to infinity from |q| = sqrt(R_d)
 template <typename T>
 __device__ __forceinline__ Node<T> detour_node(const KParams &kp, int k, C<T> eth, C<T> eD,
-                                               C<T> yp, C<T> x)
+                                               const DetourPre<T> &dp)
 {
     const int ns = kp.n_s;
-    T ap = tsqrt(cabs2(yp));
-    C<T> u = (rcp(ap)) * yp;
-    T r = T(kp.r_detour);
-    T Rd = tsqrt(cabs2(x)) + T(20);
-    if (k >= 3 * ns) return ray_node<T>(kp, k - 3 * ns, eth, eD, tsqrt(Rd));
+    if (k >= 3 * ns) return ray_node<T>(kp, k - 3 * ns, eth, eD, dp.sqRd);
     T t, w;
     if (k < ns) {
         load2<T>(kp, 1, k, t, w);
-        C<T> q1 = csqrt_p((ap - r) * u);
+        const C<T> q1 = dp.q1;
         C<T> q = t * q1;
         Node<T> n;
         n.y = q * q;
@@ -450,17 +483,13 @@ __device__ __forceinline__ Node<T> detour_node(const KParams &kp, int k, C<T> et
         T cs, sn;
         load2<T>(kp, 2, k - ns, cs, sn);
         // theta = th0 + sg pi t with e^{i th0} = -u, sg = sign(Im yp)
-        T sg = yp.i > T(0) ? T(1) : T(-1);
-        C<T> e = cx<T>(-u.r, -u.i) * cx<T>(cs, sg * sn);
-        C<T> y = yp + r * e;
-        C<T> dy = (sg * T(PI_D()) * r * w) * cx<T>(-e.i, e.r);   // i r e dtheta
+        C<T> e = cx<T>(-dp.u.r, -dp.u.i) * cx<T>(cs, dp.sg * sn);
+        C<T> y = dp.yp + dp.r * e;
+        C<T> dy = (dp.sgpr * w) * cx<T>(-e.i, e.r);   // i r e dtheta
         return finish_y_node<T>(kp, y, dy);
     }
     load2<T>(kp, 1, k - 2 * ns, t, w);
-    C<T> y0 = (ap + r) * u;
-    C<T> y1 = Rd * (eth * eth);
-    C<T> d = y1 - y0;
-    return finish_y_node<T>(kp, y0 + t * d, w * d);
+    return finish_y_node<T>(kp, dp.y0 + t * dp.d, w * dp.d);
 }
 
 // ----------------------------------------------------------------------------
@@ -710,6 +739,35 @@ __device__ __forceinline__ C<df> exact_S<df>(int dim, C<df> v, C<df> w)
     return C<df>{df(r.r), df(r.i)};
 }
 
+// Omega1, delta and the dressed pole and residue as T, read from the kernel
+// parameters (constant-bank operands): binary64 from the binary64 fields,
+// the other arithmetics from copies the host stores in their own type, so
+// that no node converts binary64 on the FP64 pipe.
+template <typename T>
+struct KConst;
+template <>
+struct KConst<double> {
+    static __device__ __forceinline__ double om1(const KParams &kp) { return kp.Omega1; }
+    static __device__ __forceinline__ double del(const KParams &kp) { return kp.delta; }
+    static __device__ __forceinline__ C<double> yp(const KParams &kp) { return {kp.pc.yp_re, kp.pc.yp_im}; }
+    static __device__ __forceinline__ C<double> Rp(const KParams &kp) { return {kp.pc.Rp_re, kp.pc.Rp_im}; }
+};
+template <>
+struct KConst<float> {
+    static __device__ __forceinline__ float om1(const KParams &kp) { return kp.f32c[0]; }
+    static __device__ __forceinline__ float del(const KParams &kp) { return kp.f32c[1]; }
+    static __device__ __forceinline__ C<float> yp(const KParams &kp) { return {kp.f32c[2], kp.f32c[3]}; }
+    static __device__ __forceinline__ C<float> Rp(const KParams &kp) { return {kp.f32c[4], kp.f32c[5]}; }
+};
+template <>
+struct KConst<df> {
+    static __device__ __forceinline__ df g(const KParams &kp, int i) { return df(kp.dfc[2 * i], kp.dfc[2 * i + 1]); }
+    static __device__ __forceinline__ df om1(const KParams &kp) { return g(kp, 0); }
+    static __device__ __forceinline__ df del(const KParams &kp) { return g(kp, 1); }
+    static __device__ __forceinline__ C<df> yp(const KParams &kp) { return {g(kp, 2), g(kp, 3)}; }
+    static __device__ __forceinline__ C<df> Rp(const KParams &kp) { return {g(kp, 4), g(kp, 5)}; }
+};
+
 // Per-pass constants of one point, computed once and reused for every node.
 template <typename T, int NT>
 struct PassPre {
@@ -720,6 +778,8 @@ struct PassPre {
     int full[NT];     // k-leg is the whole dressed propagator
     int same[NT];     // k-leg and (p-k)-leg share the pole: one reciprocal
 };
+
+
 
 template <typename T, int NT>
 __device__ __forceinline__ PassPre<T, NT> pass_pre(const KParams &kp, const Plan<T> &P, int pass,
@@ -799,7 +859,7 @@ __device__ __forceinline__ C<T> node_value(const KParams &kp, const AngTab<T, ta
     } else {
         npairs = pair_sums<T, NP, NT>(kp, tab, kp.npair, stab, srules, w, A, B, qmin) * pp.nt;
     }
-    const T Om1 = T(kp.Omega1), del = T(kp.delta);
+    const T Om1 = KConst<T>::om1(kp), del = KConst<T>::del(kp);
     C<T> sum = {T(0), T(0)};
     T mag = T(0), magk = T(0);
 #pragma unroll
@@ -820,8 +880,7 @@ __device__ __forceinline__ C<T> node_value(const KParams &kp, const AngTab<T, ta
         if (pp.same[s]) {
             p1 = pq;
         } else if (pp.full[s]) {
-            C<T> yp = cvt<T>(kp.pc.yp_re, kp.pc.yp_im);
-            C<T> Rp = cvt<T>(kp.pc.Rp_re, kp.pc.Rp_im);
+            const C<T> yp = KConst<T>::yp(kp), Rp = KConst<T>::Rp(kp);
             p1 = nd.sc * (Rp * cinv(nd.y - yp) + conj(Rp) * cinv(nd.y - conj(yp)));
         } else {
             p1 = nd.sc * cinv(nd.y + pp.m2k[s]);
@@ -836,7 +895,7 @@ __device__ __forceinline__ C<T> node_value(const KParams &kp, const AngTab<T, ta
             if (pp.same[s]) {
                 kk = kq;
             } else if (pp.full[s]) {
-                C<T> yp = cvt<T>(kp.pc.yp_re, kp.pc.yp_im);
+                const C<T> yp = KConst<T>::yp(kp);
                 kk = ay * (rcp(cabs1(nd.y - yp)) + rcp(cabs1(nd.y - conj(yp))));
             } else {
                 kk = ay * rcp(cabs1(nd.y + pp.m2k[s]));
@@ -931,8 +990,14 @@ __device__ __forceinline__ void run_pass(const KParams &kp, const AngTab<T, tab_
     const PassPre<T, NTT> pp = pass_pre<T, NTT>(kp, P, pass, x);
     const bool ray = P.kind[pass] == PASS_RAY;
     const int nn = ray ? kp.n_r : 3 * kp.n_s + kp.n_r;
+    DetourPre<T> *dps = detour_slot<T>();
+    if (!ray) {
+        __syncwarp();
+        if (lane == 0) *dps = detour_pre<T>(kp, P.eth, P.yp, x);
+        __syncwarp();
+    }
     for (int k = lane; k < nn; k += 32) {
-        Node<T> nd = !ray ? detour_node<T>(kp, k, P.eth, eD, P.yp, x)
+        Node<T> nd = !ray ? detour_node<T>(kp, k, P.eth, eD, *dps)
                           : ((CL && P.clus) ? ray_node_cl<T>(kp, k, P.eth, eD, P.cl_c, P.cl_d, P.cl_eta)
                                             : ray_node<T>(kp, k, P.eth, eD, T(0)));
         T qm;
@@ -1017,9 +1082,32 @@ __device__ __forceinline__ void eval_point(const KParams &kp, const AngTab<T, ta
         for (int o = 16; o > 0; o >>= 1) pw += __shfl_xor_sync(0xffffffffu, pw, o);
         if (lane == 0) atomicAdd(kp.pair_count, pw);
     }
-    double sr = warp_sum((double)acc.sr + (double)acc.cr);
-    double si = warp_sum((double)acc.si + (double)acc.ci);
-    double cond = kp.K_D * (sqrt(warp_sum((double)ea.s2)) + warp_sum((double)ea.s1));
+    double sr, si, cond;
+    if constexpr (std::is_same<T, float>::value) {
+        // binary32 throughout (the FP64 pipe is 1/64 of the binary32 one): the
+        // lanes' compensated sums (hi, lo) are reduced as pairs, TwoSum on the
+        // high parts; the error scale needs no more than binary32
+        float hr = acc.sr, lr = acc.cr, hi = acc.si, li = acc.ci, s1 = ea.s1, s2 = ea.s2;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            float ohr = __shfl_xor_sync(0xffffffffu, hr, o), olr = __shfl_xor_sync(0xffffffffu, lr, o);
+            float ohi = __shfl_xor_sync(0xffffffffu, hi, o), oli = __shfl_xor_sync(0xffffffffu, li, o);
+            float cr = 0.0f, ci = 0.0f;
+            two_sum_add(hr, cr, ohr);
+            two_sum_add(hi, ci, ohi);
+            lr = lr + olr + cr;
+            li = li + oli + ci;
+            s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+            s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+        }
+        sr = (double)hr + (double)lr;
+        si = (double)hi + (double)li;
+        cond = kp.K_D * ((double)sqrtf(s2) + (double)s1);
+    } else {
+        sr = warp_sum((double)acc.sr + (double)acc.cr);
+        si = warp_sum((double)acc.si + (double)acc.ci);
+        cond = kp.K_D * (sqrt(warp_sum((double)ea.s2)) + warp_sum((double)ea.s1));
+    }
     float qpt = (float)qall;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) qpt = fminf(qpt, __shfl_xor_sync(0xffffffffu, qpt, o));
