@@ -39,8 +39,8 @@ MASSES2 = (0.25, 1.0, 4.0)          # m in {0.5, 1, 2}
 NR, NA = 2048, 256
 FLOP_PER_NODE_EVAL = 11              # 22 flops per +-psi pair (9 FMA + 4 MUL)
 # DRAM bytes per point of the FP64 evaluation kernel (ncu, one 256x256 launch of the
-# current kernel: 236,800 B read, 0 B written back before the launch ended)
-TRAFFIC_PER_POINT = 236800 / 65536
+# current kernel: 233,984 B read, 0 B written back before the launch ended)
+TRAFFIC_PER_POINT = 233984 / 65536
 SM_COUNT = 152
 SM_MAX_MHZ = 2070.0
 FP64_FMA_PER_SM_CLK = 2              # nominal GB300 FP64 rate (1.25 TFLOP/s)
@@ -220,7 +220,10 @@ def run_gfc(args):
     side = args.side
     rect, _ = shard_rows(rank, ws, side)
     grid = gfc.make_grid(*rect, side, side)
-    par64 = gfc.make_params(dim=4, mu2=1.0, n_radial=NR, n_angular=NA, precision="fp64")
+    # --quick --precision P times the headline workload in precision P (for
+    # profiling the other kernels on a small case); the full line is FP64
+    par64 = gfc.make_params(dim=4, mu2=1.0, n_radial=NR, n_angular=NA,
+                            precision=args.precision if args.quick else "fp64")
     parmx = gfc.make_params(dim=4, mu2=1.0, n_radial=NR, n_angular=NA, precision="mixed")
     props = [gfc.make_prop({"kind": "scalar", "m2": m2}) for m2 in MASSES2]
     outs = [torch.empty((side, side), dtype=torch.complex128, device=dev) for _ in MASSES2]
@@ -286,7 +289,8 @@ def run_gfc(args):
     if args.quick:
         if rank == 0:
             print(json.dumps({"metric": METRIC, "value": ws * npts_step * args.steps / t64,
-                              "unit": "points/s", "quick": True, "side": side}), flush=True)
+                              "unit": "points/s", "quick": True, "side": side,
+                              "precision": args.precision}), flush=True)
         return 0
 
     # ---- mixed precision study --------------------------------------------
@@ -408,7 +412,7 @@ def run_gfc(args):
                      "achieved": achieved, "peak": peak64, "unit": "TFLOP/s",
                      "frac": achieved / peak64, "traffic": TRAFFIC_PER_POINT * side * side,
                      "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one "
-                                       "256x256 launch (236,800 B), scaled by points per launch",
+                                       "256x256 launch (233,984 B), scaled by points per launch",
                      "peak_source": "derived: 152 SM x 2 FP64 FMA/clk x 2 flop x 2070 MHz "
                                     "(ncu: dfma peak_sustained 304/clk = 152 x 2)",
                      "algorithmic": "11 flop per node-eval (22 per +-psi pair)",
@@ -479,6 +483,8 @@ def main():
                     help="grid side per GPU (the benchmark workload is 1024)")
     ap.add_argument("--quick", action="store_true",
                     help="FP64 timing only (profiling runs)")
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "f32x2", "mixed"],
+                    help="with --quick: the precision of the timed workload")
     ap.add_argument("--serve", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=2000)
     ap.add_argument("--serve-rate", type=float, default=200.0)
