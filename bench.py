@@ -20,6 +20,7 @@ the oracle's CPU throughput.
 from __future__ import annotations
 
 import argparse
+import datetime
 import json
 import os
 import subprocess
@@ -67,9 +68,12 @@ def shard_rows(rank: int, world: int, side: int = None):
 
 
 class ClockSampler:
-    """nvidia-smi samples of SM clock and throttle reasons while running."""
+    """nvidia-smi samples of SM clock and throttle reasons while running.
+    Started before the warm-up (its start-up can stall the GPU briefly, which
+    must not fall into a timed region); stop(t0, t1) keeps the samples whose
+    nvidia-smi timestamp lies in the timed window [t0, t1] (local time)."""
 
-    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    QUERY = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
@@ -93,7 +97,7 @@ class ClockSampler:
         for line in self.proc.stdout:
             self.lines.append(line.strip())
 
-    def stop(self):
+    def stop(self, t0=None, t1=None):
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         self.proc.terminate()
@@ -105,14 +109,21 @@ class ClockSampler:
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for ln in self.lines:
             f = [t.strip() for t in ln.split(",")]
-            if len(f) < 9:
+            if len(f) < 10:
                 continue
+            if t0 is not None:
+                try:
+                    ts = datetime.datetime.strptime(f[0], "%Y/%m/%d %H:%M:%S.%f")
+                except ValueError:
+                    continue
+                if not (t0 <= ts <= t1):
+                    continue
             try:
-                sm.append(float(f[1]))
-                smax.append(float(f[2]))
+                sm.append(float(f[2]))
+                smax.append(float(f[3]))
             except ValueError:
                 continue
-            for nm, v in zip(names, f[5:9]):
+            for nm, v in zip(names, f[6:10]):
                 if v.lower() == "active":
                     reasons.add(nm)
         return {"sm_mhz": float(np.median(sm)) if sm else None,
@@ -257,13 +268,14 @@ def run_gfc(args):
                 gfc.eval_grid(p, params, grid, out=G, stream=stream)
 
     def timed(params, steps, warmup, per_launch=None, clocks=None):
+        if clocks:
+            clocks.start()
         for _ in range(warmup):
             step(params)
         torch.cuda.synchronize()
         barrier()
         torch.cuda.synchronize()
-        if clocks:
-            clocks.start()
+        tw0 = datetime.datetime.now()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
@@ -272,9 +284,10 @@ def run_gfc(args):
             step(params, per_launch)
         e1.record(stream)
         torch.cuda.synchronize()
+        tw1 = datetime.datetime.now()
         barrier()
         torch.cuda.synchronize()
-        ck = clocks.stop() if clocks else None
+        ck = clocks.stop(tw0, tw1) if clocks else None
         return max_over_ranks(e0.elapsed_time(e1) / 1e3), ck
 
     # ---- FP64: the headline ------------------------------------------------
@@ -290,7 +303,8 @@ def run_gfc(args):
         if rank == 0:
             print(json.dumps({"metric": METRIC, "value": ws * npts_step * args.steps / t64,
                               "unit": "points/s", "quick": True, "side": side,
-                              "precision": args.precision}), flush=True)
+                              "precision": args.precision,
+                              "launch_ms": [round(v, 3) for v in launch_ms]}), flush=True)
         return 0
 
     # ---- mixed precision study --------------------------------------------

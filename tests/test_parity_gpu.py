@@ -317,3 +317,24 @@ def test_clustered_near_axis_band():
     torch.cuda.synchronize()
     ref = oracle.eval_points(SCALAR, oracle_params(par), x)
     assert_parity(G.cpu().numpy(), ref, RTOL["fp64"], x, "clustered near-axis band")
+
+
+_MAX_X = np.array([2 + 1j, -2 + 0.3j, -8 - 2j, 0.5 - 4j, -0.2 + 0.01j, 3.9 + 0.2j, -6 + 0.2j,
+                   1e-3 + 1e-3j])
+_MAX_REF = {}
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed", "f32x2"])
+@pytest.mark.parametrize("name", ["scalar", "paper"])
+def test_maximum_orders(name, precision):
+    """The largest orders the library accepts: 16384 radial x 512 angular
+    nodes (256 pairs: generic pair loop, the largest compressed rules), on
+    points of every contour kind of the bubble and the paper's pair."""
+    prop, mu2 = (SCALAR, 1.0) if name == "scalar" else (PAPER, 0.0)
+    par = dict(dim=4, mu2=mu2, n_radial=16384, n_angular=512, precision=precision)
+    G = gfc.eval_points(prop, par, torch.tensor(_MAX_X, device="cuda"))
+    torch.cuda.synchronize()
+    if name not in _MAX_REF:
+        _MAX_REF[name] = oracle.eval_points(prop, oracle_params(par), _MAX_X)
+    assert_parity(G.cpu().numpy(), _MAX_REF[name], RTOL[precision], _MAX_X,
+                  f"max orders {name} {precision}")
