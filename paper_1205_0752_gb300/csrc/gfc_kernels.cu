@@ -42,8 +42,8 @@ g0mu_kernel(const __grid_constant__ KParams kp,
         double qm;
         int np;
         C<double> v = P.nterm[0] == 2
-                          ? node_value<double, NP, 2, 1>(kp, tab, stab, srules, pp2, x, nd, ea, qm, np)
-                          : node_value<double, NP, 1, 1>(kp, tab, stab, srules, pp1, x, nd, ea, qm, np);
+                          ? node_value<double, NP, 2, 1>(kp, tab, stab, srules, pp2, x, nd, ea, qm, np, false)
+                          : node_value<double, NP, 1, 1>(kp, tab, stab, srules, pp1, x, nd, ea, qm, np, false);
         sr += v.r;
         si += v.i;
     }

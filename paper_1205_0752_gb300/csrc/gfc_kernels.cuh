@@ -37,6 +37,11 @@ namespace gfc {
 // the nodes' error scale), from binary32-vs-FP64 runs over the test grids
 constexpr double kMixedErrFactor = 2.0;
 constexpr float kMixedPinchQ = 1e-5f;   // |1 - w t|^2 below which a point is routed
+// weight of the pole terms of kappa on binary32 ray nodes with y exact
+#ifndef GFC_POLE_WEIGHT
+#define GFC_POLE_WEIGHT 0.5
+#endif
+constexpr double kMixedPoleWeight = GFC_POLE_WEIGHT;
 
 // ----------------------------------------------------------------------------
 // complex arithmetic
@@ -277,6 +282,8 @@ struct Node {
     C<T> y;
     C<T> Jt;    // measure / (1 + |y|)^2
     T sc;       // 1 + |y|
+    C<T> ylo;   // binary32 ray nodes: y's rounding remainder (y = y + ylo exactly
+                // for the node |q| = rho_hi + rho_lo on the ray e2); else 0
 };
 
 template <typename T>
@@ -340,7 +347,35 @@ __device__ __forceinline__ Node<T> ray_node(const KParams &kp, int k, C<T> eth, 
 {
     T rho, W;
     load2<T>(kp, 0, k, rho, W);
-    return ray_node_at<T>(kp, rho + rho0, W, eth, eD);
+    Node<T> n = ray_node_at<T>(kp, rho + rho0, W, eth, eD);
+    n.ylo = {T(0), T(0)};
+    return n;
+}
+
+// binary32 node k of the ray from q = 0, with y exact: |q| = rho_hi + rho_lo
+// from the double-float table, rho^2 = p + pe by an FMA TwoProduct, and
+// y = p e2 + pe e2 split into its rounded value and remainder (TwoProduct
+// again), so that y + M2 and a = x + y + M2 can be formed with one rounding
+// each (the contour passes close to y = -M2 next to the negative real axis,
+// where y + M2 cancels).
+__device__ __forceinline__ Node<float> ray_node_exact_y(const KParams &kp, int k, C<float> e2,
+                                                        C<float> eD)
+{
+    const float4 v = __ldg(kp.rad_df + k);
+    const float rh = v.x, rl = v.y, W = v.z;
+    const float p = rh * rh;
+    const float pe = fmaf(rh, rh, -p) + 2.0f * rh * rl;
+    Node<float> n;
+    n.y.r = p * e2.r;
+    n.y.i = p * e2.i;
+    n.ylo.r = fmaf(p, e2.r, -n.y.r) + pe * e2.r;
+    n.ylo.i = fmaf(p, e2.i, -n.y.i) + pe * e2.i;
+    n.sc = 1.0f + p;
+    float s = rcp(n.sc);
+    s = s * s;
+    const float rs = p * s;
+    n.Jt = ((kp.dim == 4 ? rs * rh : rs) * W) * eD;
+    return n;
 }
 
 // node k of the clustered ray: n_s nodes on [0, c] and on [c, 2c] with
@@ -397,7 +432,9 @@ __device__ __forceinline__ Node<T> ray_node_cl(const KParams &kp, int k, C<T> et
 {
     T rho, W;
     cl_rho_w(kp, k, c, d, eta, rho, W);
-    return ray_node_at<T>(kp, rho, W, eth, eD);
+    Node<T> n = ray_node_at<T>(kp, rho, W, eth, eD);
+    n.ylo = {T(0), T(0)};
+    return n;
 }
 
 template <typename T>
@@ -413,6 +450,7 @@ __device__ __forceinline__ Node<T> finish_y_node(const KParams &kp, C<T> y, C<T>
 {
     Node<T> n;
     n.y = y;
+    n.ylo = {T(0), T(0)};
     n.sc = T(1) + tsqrt(cabs2(y));
     T s = rcp(n.sc);
     s = s * s;
@@ -470,6 +508,7 @@ __device__ __forceinline__ Node<T> detour_node(const KParams &kp, int k, C<T> et
         C<T> q = t * q1;
         Node<T> n;
         n.y = q * q;
+        n.ylo = {T(0), T(0)};
         n.sc = T(1) + cabs2(q);
         T s = rcp(n.sc);
         s = s * s;
@@ -777,6 +816,7 @@ struct PassPre {
     C<T> omx[NT];     // Omega (x + M2_t)
     int full[NT];     // k-leg is the whole dressed propagator
     int same[NT];     // k-leg and (p-k)-leg share the pole: one reciprocal
+    C<T> xm[NT], xml[NT];   // binary32: x + M2_t rounded, and its remainder (TwoSum)
 };
 
 
@@ -797,6 +837,14 @@ __device__ __forceinline__ PassPre<T, NT> pass_pre(const KParams &kp, const Plan
         pp.omx[s] = Om * (x + tm.m2q);
         pp.full[s] = tm.full;
         pp.same[s] = !tm.full && tm.m2k.r == tm.m2q.r && tm.m2k.i == tm.m2q.i;
+        if constexpr (std::is_same<T, float>::value) {
+            // TwoSum (Knuth): x + M2 = xm + xml exactly
+            const C<T> m = tm.m2q;
+            const T sr = x.r + m.r, si = x.i + m.i;
+            const T br = sr - x.r, bi = si - x.i;
+            pp.xm[s] = {sr, si};
+            pp.xml[s] = {(x.r - (sr - br)) + (m.r - br), (x.i - (si - bi)) + (m.i - bi)};
+        }
     }
     return pp;
 }
@@ -830,8 +878,14 @@ template <typename T, int NP, int NT, int V>
 __device__ __forceinline__ C<T> node_value(const KParams &kp, const AngTab<T, tab_size<NP>()> &tab,
                                            const T *stab, const void *srules,
                                            const PassPre<T, NT> &pp, C<T> x, const Node<T> &nd,
-                                           ErrAcc<T> &ea, T &qmin, int &npairs)
+                                           ErrAcc<T> &ea, T &qmin, int &npairs, bool exact_y)
 {
+    constexpr bool f32 = std::is_same<T, float>::value;
+    // y + c formed with one rounding from y's remainder (binary32), else plain
+    auto ypc = [&](C<T> c) -> C<T> {
+        if constexpr (f32) return C<T>{(nd.y.r + c.r) + nd.ylo.r, (nd.y.i + c.i) + nd.ylo.i};
+        else return nd.y + c;
+    };
     // double-float has no error-scale output (it would cost registers)
     const bool want_mag = std::is_same<T, float>::value ||
                           (std::is_same<T, double>::value && kp.cond_out != nullptr);
@@ -839,7 +893,12 @@ __device__ __forceinline__ C<T> node_value(const KParams &kp, const AngTab<T, ta
     T kap[NT];
 #pragma unroll
     for (int s = 0; s < NT; ++s) {
-        C<T> a = x + nd.y + pp.m2q[s];
+        C<T> a;
+        if constexpr (f32)
+            a = {(pp.xm[s].r + nd.y.r) + (pp.xml[s].r + nd.ylo.r),
+                 (pp.xm[s].i + nd.y.i) + (pp.xml[s].i + nd.ylo.i)};
+        else
+            a = x + nd.y + pp.m2q[s];
         ia[s] = cinv(a);
         v[s] = T(4) * (nd.y * ia[s]);
         w[s] = (x * v[s]) * ia[s];
@@ -875,22 +934,23 @@ __device__ __forceinline__ C<T> node_value(const KParams &kp, const AngTab<T, ta
             S = lead + vw * T2;
         }
         // (1 + |y|)^2 P1(y) / (y + M2)
-        C<T> pq = nd.sc * cinv(nd.y + pp.m2q[s]);
+        const C<T> ypq = ypc(pp.m2q[s]);
+        C<T> pq = nd.sc * cinv(ypq);
         C<T> p1;
         if (pp.same[s]) {
             p1 = pq;
         } else if (pp.full[s]) {
             const C<T> yp = KConst<T>::yp(kp), Rp = KConst<T>::Rp(kp);
-            p1 = nd.sc * (Rp * cinv(nd.y - yp) + conj(Rp) * cinv(nd.y - conj(yp)));
+            p1 = nd.sc * (Rp * cinv(ypc(C<T>{-yp.r, -yp.i})) + conj(Rp) * cinv(ypc(C<T>{-yp.r, yp.i})));
         } else {
-            p1 = nd.sc * cinv(nd.y + pp.m2k[s]);
+            p1 = nd.sc * cinv(ypc(pp.m2k[s]));
         }
         C<T> f = (pp.cx2[s] * (p1 * pq)) * ia[s];
         C<T> fS = f * S;
         sum = sum + fS;
         if (want_mag) {
             const T ay = cabs1(nd.y);
-            T kq = ay * rcp(cabs1(nd.y + pp.m2q[s]));
+            T kq = ay * rcp(cabs1(ypq));
             T kk;
             if (pp.same[s]) {
                 kk = kq;
@@ -902,7 +962,10 @@ __device__ __forceinline__ C<T> node_value(const KParams &kp, const AngTab<T, ta
             }
             const T m = cabs1(fS);
             mag += m;
-            magk += m * (kap[s] + kq + kk);
+            // with y, y + M2 and a exact to one rounding (binary32 ray nodes)
+            // the pole terms weigh less: what remains is the rounding of the
+            // node's later operations near the pole, not the cancellation
+            magk += m * (kap[s] + kq + kk) * (exact_y ? T(kMixedPoleWeight) : T(1));
         }
     }
     if (want_mag) {
@@ -984,7 +1047,7 @@ __device__ __forceinline__ void point_x(const KParams &kp, int64_t p, double &xr
 template <typename T, int NP, int NTT, int CL>
 __device__ __forceinline__ void run_pass(const KParams &kp, const AngTab<T, tab_size<NP>()> &tab,
                                          const T *stab, const void *srules, const Plan<T> &P,
-                                         int pass, C<T> x, C<T> eD, int lane, Acc<T> &acc,
+                                         int pass, C<T> x, C<T> e2, C<T> eD, int lane, Acc<T> &acc,
                                          ErrAcc<T> &ea, T &qall, int &pairs)
 {
     const PassPre<T, NTT> pp = pass_pre<T, NTT>(kp, P, pass, x);
@@ -996,13 +1059,21 @@ __device__ __forceinline__ void run_pass(const KParams &kp, const AngTab<T, tab_
         if (lane == 0) *dps = detour_pre<T>(kp, P.eth, P.yp, x);
         __syncwarp();
     }
+    // binary32 mapped rays from q = 0 use nodes with y exact (see ray_node_exact_y)
+    const bool exact_y = std::is_same<T, float>::value && ray && !(CL && P.clus);
     for (int k = lane; k < nn; k += 32) {
-        Node<T> nd = !ray ? detour_node<T>(kp, k, P.eth, eD, *dps)
-                          : ((CL && P.clus) ? ray_node_cl<T>(kp, k, P.eth, eD, P.cl_c, P.cl_d, P.cl_eta)
-                                            : ray_node<T>(kp, k, P.eth, eD, T(0)));
+        Node<T> nd;
+        if (!ray)
+            nd = detour_node<T>(kp, k, P.eth, eD, *dps);
+        else if (CL && P.clus)
+            nd = ray_node_cl<T>(kp, k, P.eth, eD, P.cl_c, P.cl_d, P.cl_eta);
+        else if constexpr (std::is_same<T, float>::value)
+            nd = ray_node_exact_y(kp, k, e2, eD);
+        else
+            nd = ray_node<T>(kp, k, P.eth, eD, T(0));
         T qm;
         int np;
-        C<T> v = node_value<T, NP, NTT, CL>(kp, tab, stab, srules, pp, x, nd, ea, qm, np);
+        C<T> v = node_value<T, NP, NTT, CL>(kp, tab, stab, srules, pp, x, nd, ea, qm, np, exact_y);
         acc_add(acc, v);
         qall = fmin(qall, qm);
         pairs += np;
@@ -1028,10 +1099,10 @@ __device__ __forceinline__ int point_sum(const KParams &kp, const AngTab<T, tab_
         if (pass >= P.npass) break;
         total += P.kind[pass] == PASS_RAY ? kp.n_r : 3 * kp.n_s + kp.n_r;
         if (NT > 1 && P.nterm[pass] == 2)
-            run_pass<T, NP, (NT > 1 ? 2 : 1), CL>(kp, tab, stab, srules, P, pass, x, eD, lane,
+            run_pass<T, NP, (NT > 1 ? 2 : 1), CL>(kp, tab, stab, srules, P, pass, x, e2, eD, lane,
                                                  acc, ea, qall, pairs);
         else
-            run_pass<T, NP, 1, CL>(kp, tab, stab, srules, P, pass, x, eD, lane, acc, ea, qall,
+            run_pass<T, NP, 1, CL>(kp, tab, stab, srules, P, pass, x, e2, eD, lane, acc, ea, qall,
                                    pairs);
     }
     return total;
