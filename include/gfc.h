@@ -245,6 +245,15 @@ int gfc_eval_points_noalloc(const gfc_propagator *prop, const gfc_params *params
 int gfc_angular_map(const gfc_propagator *prop, const gfc_params *params, double x_re,
                     double x_im, const double *y, int64_t ny, double *B, void *stream);
 
+/* Test hook (host-side fault injection; the paper has no counterpart): the
+ * next n device allocations the library makes -- node tables, per-stream
+ * scratch, mixed-precision lists, host-path staging, serving buffers -- fail
+ * as if the runtime had reported cudaErrorMemoryAllocation, so that error
+ * paths can be exercised without faulting a GPU. The failing call returns
+ * GFC_ECUDA with the failure in gfc_last_error(); n = 0 clears the hook.
+ * GFC_EINVAL for n < 0. */
+int gfc_test_fail_allocations(int n);
+
 /* gfc_region_map: region 1 of Fig. 2. For each of npts external x (DEVICE
  * complex128), free_out[i] (DEVICE int32) = 1 if the branch cut of B(x, .)
  * -- the curve y = (sqrt(x) cos th +- sqrt(-x sin^2 th - M2))^2, th in

@@ -99,6 +99,7 @@ _SIGS = {
     "gfc_angular_map": ([ctypes.POINTER(_Prop), ctypes.POINTER(_Params), ctypes.c_double,
                          ctypes.c_double, _P, ctypes.c_int64, _P, _P], ctypes.c_int),
     "gfc_region_map": ([ctypes.POINTER(_Prop), _P, ctypes.c_int64, _P, _P], ctypes.c_int),
+    "gfc_test_fail_allocations": ([ctypes.c_int], ctypes.c_int),
 }
 
 _lib = None
@@ -401,3 +402,9 @@ def region_map(prop, x, out=None, stream=None):
                               x.numel(), ctypes.c_void_p(F.data_ptr()), _stream_ptr(stream)),
            "gfc_region_map")
     return F
+
+
+def test_fail_allocations(n: int):
+    """Test hook: the next ``n`` device allocations of the library fail
+    (gfc_test_fail_allocations); 0 clears it."""
+    _check(load_library().gfc_test_fail_allocations(int(n)), "gfc_test_fail_allocations")

@@ -2,6 +2,7 @@
 // launch sequence of one evaluation (G0(mu2) first, then the points).
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cmath>
 #include <complex>
 #include <cstdio>
@@ -15,6 +16,8 @@
 
 #include "gfc.h"
 #include "gfc_df.h"
+
+#include <nvtx3/nvToolsExt.h>
 #include "gfc_internal.h"
 
 namespace gfc {
@@ -38,6 +41,36 @@ int cuda_fail(cudaError_t e, const char *what)
     return fail(GFC_ECUDA, std::string(what) + ": " + cudaGetErrorName(e) + " (" +
                                cudaGetErrorString(e) + ")");
 }
+
+// test hook: the next g_fail_allocs device allocations fail (host-side fault
+// injection; the GPU is never faulted)
+static std::atomic<int> g_fail_allocs{0};
+
+static bool take_injected_failure()
+{
+    int v = g_fail_allocs.load();
+    while (v > 0 && !g_fail_allocs.compare_exchange_weak(v, v - 1)) {
+    }
+    return v > 0;
+}
+
+cudaError_t dev_malloc(void **p, size_t bytes)
+{
+    if (take_injected_failure()) return cudaErrorMemoryAllocation;
+    return cudaMalloc(p, bytes);
+}
+
+cudaError_t dev_malloc_async(void **p, size_t bytes, cudaStream_t s)
+{
+    if (take_injected_failure()) return cudaErrorMemoryAllocation;
+    return cudaMallocAsync(p, bytes, s);
+}
+
+// NVTX range for the duration of one ABI call (a no-op without a tool)
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+};
 
 // ---------------------------------------------------------------------------
 // Gauss-Legendre rule on [-1, 1] (Abramowitz & Stegun 25.4.29), computed by
@@ -329,7 +362,7 @@ template <typename V>
 static int upload(V **dst, const std::vector<V> &src, size_t &bytes)
 {
     size_t nb = sizeof(V) * src.size();
-    cudaError_t e = cudaMalloc((void **)dst, nb ? nb : sizeof(V));
+    cudaError_t e = dev_malloc((void **)dst, nb ? nb : sizeof(V));
     if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(node table)");
     if (nb) {
         e = cudaMemcpy(*dst, src.data(), nb, cudaMemcpyHostToDevice);
@@ -530,10 +563,10 @@ int get_scratch(int dev, cudaStream_t s, Scratch **out)
     }
     auto S = std::make_unique<Scratch>();
     cudaError_t e;
-    if ((e = cudaMalloc((void **)&S->partials, sizeof(double) * 2 * kMaxG0Warps)) != cudaSuccess ||
-        (e = cudaMalloc((void **)&S->ticket, sizeof(unsigned))) != cudaSuccess ||
-        (e = cudaMalloc((void **)&S->g0mu, sizeof(double) * 2)) != cudaSuccess ||
-        (e = cudaMalloc((void **)&S->counters, sizeof(unsigned long long) * kCounters)) != cudaSuccess) {
+    if ((e = dev_malloc((void **)&S->partials, sizeof(double) * 2 * kMaxG0Warps)) != cudaSuccess ||
+        (e = dev_malloc((void **)&S->ticket, sizeof(unsigned))) != cudaSuccess ||
+        (e = dev_malloc((void **)&S->g0mu, sizeof(double) * 2)) != cudaSuccess ||
+        (e = dev_malloc((void **)&S->counters, sizeof(unsigned long long) * kCounters)) != cudaSuccess) {
         cudaFree(S->partials);
         cudaFree(S->ticket);
         cudaFree(S->g0mu);
@@ -704,7 +737,7 @@ static int grow_list(Scratch &S, int64_t n)
     cudaFree(S.list);
     S.list = nullptr;
     S.list_cap = 0;
-    cudaError_t e = cudaMalloc((void **)&S.list, sizeof(int64_t) * (n > 0 ? n : 1));
+    cudaError_t e = dev_malloc((void **)&S.list, sizeof(int64_t) * (n > 0 ? n : 1));
     if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(binary64 list)");
     S.list_cap = n;
     return GFC_OK;
@@ -727,6 +760,7 @@ static DevTables dev_tables(const Tables &T)
 static int run(const gfc_propagator *prop, const gfc_params *p, KParams kp_points,
                cudaStream_t st, double *cond_out)
 {
+    NvtxRange nvtx("gfc_eval");
     PropConst pc;
     int rc = make_prop(prop, p, pc);
     if (rc) return rc;
@@ -989,8 +1023,8 @@ int gfc_eval_points_host(const gfc_propagator *prop, const gfc_params *params,
         S->stage_x = S->stage_G = nullptr;
         S->stage_cap = 0;
         cudaError_t e;
-        if ((e = cudaMalloc((void **)&S->stage_x, 16 * npts)) != cudaSuccess ||
-            (e = cudaMalloc((void **)&S->stage_G, 16 * npts)) != cudaSuccess)
+        if ((e = dev_malloc((void **)&S->stage_x, 16 * npts)) != cudaSuccess ||
+            (e = dev_malloc((void **)&S->stage_G, 16 * npts)) != cudaSuccess)
             return cuda_fail(e, "cudaMalloc(staging)");
         S->stage_cap = npts;
     }
@@ -1045,3 +1079,10 @@ int gfc_release(void)
 }
 
 }  // extern "C"
+
+extern "C" int gfc_test_fail_allocations(int n)
+{
+    if (n < 0) return gfc::fail(GFC_EINVAL, "n must be >= 0");
+    gfc::g_fail_allocs.store(n);
+    return GFC_OK;
+}

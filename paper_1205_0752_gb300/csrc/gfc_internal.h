@@ -163,6 +163,11 @@ cudaError_t launch_grid_points(double re0, double dre, double im0, double dim_im
 // ---------------------------------------------------------------------------
 struct Tables;
 int fail(int code, const char *msg);
+// Device allocations of the library go through these: they honour the test
+// hook gfc_test_fail_allocations (the next n allocations report
+// cudaErrorMemoryAllocation without calling the runtime).
+cudaError_t dev_malloc(void **p, size_t bytes);
+cudaError_t dev_malloc_async(void **p, size_t bytes, cudaStream_t s);
 int cuda_fail(cudaError_t e, const char *what);
 int check_params_c(const void *params);
 int check_grid_c(const void *grid);

@@ -15,6 +15,8 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+
+#include <nvtx3/nvToolsExt.h>
 #include <chrono>
 #include <cmath>
 #include <condition_variable>
@@ -225,11 +227,11 @@ int admit(gfc_server *s, Request *r)
     if ((rc = make_prop_c(&r->prop, &r->params, pc))) return rc;
     r->slot = s->free_slots.back();
     s->free_slots.pop_back();
-    cudaError_t e = cudaMallocAsync((void **)&r->G_dev, 16 * r->npts, s->admit_stream);
+    cudaError_t e = dev_malloc_async((void **)&r->G_dev, 16 * r->npts, s->admit_stream);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync(request output)");
     const bool mixed = r->params.precision == GFC_MIXED;
     if (mixed) {
-        e = cudaMallocAsync((void **)&r->list_dev, sizeof(int64_t) * r->npts, s->admit_stream);
+        e = dev_malloc_async((void **)&r->list_dev, sizeof(int64_t) * r->npts, s->admit_stream);
         if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync(request list)");
         e = cudaMemsetAsync(s->slot_counts_dev + r->slot, 0, sizeof(unsigned long long),
                             s->admit_stream);
@@ -366,7 +368,9 @@ void issue_launches(gfc_server *s)
         bl.rules_total = r0->kp.rules_total;
         bl.radial_rule = std::get<6>(key);
         bl.ang_exact = std::get<5>(key) == GFC_ANG_EXACT;
+        nvtxRangePushA("gfc_server_launch");
         cudaError_t e = launch_batch(bl, dev_tables_c(*r0->T), arith, std::get<3>(key) != 0, st);
+        nvtxRangePop();
         if (e != cudaSuccess) {
             s->error = GFC_ECUDA;
         }
