@@ -287,9 +287,6 @@ struct Node {
 };
 
 template <typename T>
-__device__ __forceinline__ float2 ld(const float2 *p) { return __ldg(p); }
-
-template <typename T>
 __device__ __forceinline__ void load2(const KParams &kp, int which, int k, T &a, T &b);
 
 template <>
@@ -534,11 +531,6 @@ __device__ __forceinline__ Node<T> detour_node(const KParams &kp, int k, C<T> et
 // ----------------------------------------------------------------------------
 // angular pair sum
 // ----------------------------------------------------------------------------
-template <typename T, int NT>
-struct Setup {
-    C<T> ia[NT], v[NT], w[NT];
-};
-
 // |1 - w t|^2 for one angular node. Direct form (1 - wr t)^2 + (wi t)^2: its
 // rounding error relative to the result is ~ eps/|1 - w t| next to a pinch.
 // Horner form 1 + t (|w|^2 t - 2 wr): two FMAs, error ~ eps/|1 - w t|^2, used
