@@ -203,6 +203,15 @@ def run_serve(args):
         srv.wait(t)
     wall = time.perf_counter() - t0
     st = srv.stats()
+    if args.serve_log:
+        # one JSON line per request: its parameters and the server's record
+        with open(args.serve_log, "w") as f:
+            for t, r in zip(tickets, reqs):
+                rec = {"ticket": int(t), "kind": r["prop"]["kind"], "side": r["side"],
+                       "dim": r["dim"], "n_radial": r["n_radial"], "n_angular": r["n_angular"],
+                       "precision": r["precision"], "t_arrival_s": r["t_arrival"]}
+                rec.update(srv.request_info(t))
+                f.write(json.dumps(rec) + "\n")
     srv.close()
     pts = sum(r["side"] ** 2 for r in reqs)
     line = {"metric": "serve p50/p99 ms", "value": st.p99_ms, "unit": "ms",
@@ -503,6 +512,8 @@ def main():
     ap.add_argument("--serve", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=2000)
     ap.add_argument("--serve-rate", type=float, default=200.0)
+    ap.add_argument("--serve-log", default=None,
+                    help="with --serve: write one JSON line per request to this file")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -313,6 +313,22 @@ int gfc_server_cancel(gfc_server *s, uint64_t ticket);
 
 int gfc_server_stats(gfc_server *s, gfc_stats *out);
 
+/* One request's record, for per-request logs (any time after submission). */
+typedef struct {
+    int status;               /* final status; GFC_ETIMEOUT while not finished  */
+    int state;                /* 0 queued, 1 on the device, 2 finished          */
+    int64_t points;           /* points of the grid                             */
+    int64_t points_routed;    /* MIXED: points re-evaluated by the fallback
+                                 arithmetic; -1 if not (yet) known              */
+    double queue_ms;          /* submission -> admission; -1 while queued       */
+    double total_ms;          /* submission -> completion; -1 while running     */
+    int64_t launches;         /* batched launches that carried its work         */
+    size_t bytes;             /* device bytes admitted for it                   */
+} gfc_request_info;
+
+/* GFC_ENOTFOUND for an unknown ticket. */
+int gfc_server_request_info(gfc_server *s, uint64_t ticket, gfc_request_info *out);
+
 /* Cancels what is still queued, drains what is on the device, frees all. */
 int gfc_server_destroy(gfc_server *s);
 

@@ -65,6 +65,13 @@ class _ServerStats(ctypes.Structure):
                 ("launches", ctypes.c_int64), ("queued", ctypes.c_int), ("active", ctypes.c_int)]
 
 
+class _RequestInfo(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("state", ctypes.c_int),
+                ("points", ctypes.c_int64), ("points_routed", ctypes.c_int64),
+                ("queue_ms", ctypes.c_double), ("total_ms", ctypes.c_double),
+                ("launches", ctypes.c_int64), ("bytes", ctypes.c_size_t)]
+
+
 # every symbol of include/gfc.h with (argtypes, restype)
 _P = ctypes.c_void_p
 _SIGS = {
@@ -95,6 +102,7 @@ _SIGS = {
     "gfc_server_wait": ([_P, ctypes.c_uint64, ctypes.c_int], ctypes.c_int),
     "gfc_server_cancel": ([_P, ctypes.c_uint64], ctypes.c_int),
     "gfc_server_stats": ([_P, ctypes.POINTER(_ServerStats)], ctypes.c_int),
+    "gfc_server_request_info": ([_P, ctypes.c_uint64, ctypes.POINTER(_RequestInfo)], ctypes.c_int),
     "gfc_server_destroy": ([_P], ctypes.c_int),
     "gfc_angular_map": ([ctypes.POINTER(_Prop), ctypes.POINTER(_Params), ctypes.c_double,
                          ctypes.c_double, _P, ctypes.c_int64, _P, _P], ctypes.c_int),
@@ -363,6 +371,13 @@ class Server:
         return ServerStats(s.submitted, s.completed, s.rejected, s.canceled, s.p50_ms, s.p99_ms,
                            s.points_per_s, s.points_done, s.bytes_in_use, s.bytes_budget,
                            s.launches, s.queued, s.active)
+
+    def request_info(self, ticket) -> dict:
+        """One request's record (gfc_server_request_info) as a dict."""
+        r = _RequestInfo()
+        _check(self._lib.gfc_server_request_info(self._h, ticket, ctypes.byref(r)),
+               "gfc_server_request_info")
+        return {k: getattr(r, k) for k, _ in _RequestInfo._fields_}
 
     def close(self):
         if self._h:

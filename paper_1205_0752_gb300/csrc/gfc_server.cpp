@@ -82,7 +82,10 @@ struct Request {
     size_t pinned_size = 0;
     cudaEvent_t copy_done = nullptr;
     double cost_per_point = 1.0;
-    clk::time_point t_submit, t_done;
+    clk::time_point t_submit, t_admit, t_done;
+    bool admitted = false;
+    int64_t launches = 0;               // batched launches that carried its work
+    int64_t routed = -1;                // MIXED: points re-evaluated by the fallback
 };
 
 struct LaunchRec {
@@ -275,6 +278,8 @@ int admit(gfc_server *s, Request *r)
         r->phases = {Phase{MODE_BULK32, ARITH_F32, 0, r->npts, 0}, Phase{MODE_LIST64, ar, 0, -1, 0}};
     }
     r->state = R_ACTIVE;
+    r->admitted = true;
+    r->t_admit = clk::now();
     s->active.push_back(r);
     return GFC_OK;
 }
@@ -345,6 +350,7 @@ void issue_launches(gfc_server *s)
         if (nitems == 0) continue;
         for (auto &c : count) {
             c.first.first->phases[c.first.second].items_out += c.second;
+            c.first.first->launches++;
             L.reqs.push_back(std::make_tuple(c.first.first, c.first.second, c.second));
         }
         cudaStream_t st = s->streams[s->next_stream];
@@ -403,6 +409,7 @@ bool progress(gfc_server *s)
             if (r->count_pending) {
                 if (cudaEventQuery(r->count_done) == cudaSuccess) {
                     p1.end = (int64_t)s->slot_counts_host[r->slot];
+                    r->routed = p1.end;
                     r->count_pending = false;
                     changed = true;
                 }
@@ -605,6 +612,27 @@ int gfc_server_wait(gfc_server *s, uint64_t ticket, int timeout_ms)
         return fail(GFC_ETIMEOUT, "request still running");
     }
     return r->status;
+}
+
+int gfc_server_request_info(gfc_server *s, uint64_t ticket, gfc_request_info *out)
+{
+    if (!s || !out) return fail(GFC_EINVAL, "NULL server or output");
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->reqs.find(ticket);
+    if (it == s->reqs.end()) return fail(GFC_ENOTFOUND, "unknown ticket");
+    const Request *r = it->second.get();
+    auto ms = [](clk::time_point a, clk::time_point b) {
+        return std::chrono::duration<double, std::milli>(b - a).count();
+    };
+    out->status = r->state == R_DONE ? r->status : GFC_ETIMEOUT;
+    out->state = r->state == R_QUEUED ? 0 : (r->state == R_DONE ? 2 : 1);
+    out->points = r->npts;
+    out->points_routed = r->routed;
+    out->queue_ms = r->admitted ? ms(r->t_submit, r->t_admit) : -1.0;
+    out->total_ms = r->state == R_DONE ? ms(r->t_submit, r->t_done) : -1.0;
+    out->launches = r->launches;
+    out->bytes = r->bytes;
+    return GFC_OK;
 }
 
 int gfc_server_cancel(gfc_server *s, uint64_t ticket)

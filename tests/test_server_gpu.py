@@ -69,6 +69,15 @@ def test_mix_equals_alone():
         st = srv.stats()
         assert st.completed == len(mix) and st.launches >= 2
         assert st.p99_ms >= st.p50_ms > 0
+        for (t, _), (p, q, s) in zip(tickets, mix):
+            info = srv.request_info(t)
+            assert info["status"] == 0 and info["state"] == 2 and info["points"] == s * s
+            assert 0.0 <= info["queue_ms"] <= info["total_ms"] and info["launches"] >= 1
+            assert info["bytes"] >= 16 * s * s
+            if q["precision"] == "mixed":
+                assert 0 <= info["points_routed"] <= s * s
+            else:
+                assert info["points_routed"] == -1
     for (t, G), ref, (p, q, s) in zip(tickets, alone, mix):
         assert _rel(G, ref) <= RTOL[q["precision"]], (p, q, s, _rel(G, ref))
 
