@@ -172,8 +172,9 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "impl": "reference",
-            "config": {"workload": "bubble m in {0.5,1,2}, D=4, mu2=1, 1024x1024 over "
-                                   "[-10,5]x[-5,5], 2048x256 nodes, FP64 (oracle sample)"},
+            "config": {"workload": "bubble m in {0.5,1,2}, D=4, mu2=1, 1024x1024 per GPU over "
+                                   "[-10,5]x[-5,5], 2048x256 nodes, FP64",
+                       "reference_sample": sample},
             "cpu_baseline": {"value": value, "unit": "points/s", "cores": cores,
                              "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "points/s", "h2d_bytes_per_step": 0,
