@@ -222,7 +222,10 @@ static bool tridiag_ql(int n, std::vector<double> &d, std::vector<double> sub,
 static void build_rules(Tables &T, std::vector<double> &r64, std::vector<float4> &r32)
 {
     const int N = (int)T.t.size();
-    static const int cand[] = {2, 3, 4, 6, 8, 12, 16, 24, 32, 48, 64, 96};
+    // sizes spaced by at most ~25 %, so that the smallest exact rule of a node
+    // over-provisions little
+    static const int cand[] = {2, 3, 4, 5, 6, 7, 8, 10, 12, 14, 16, 18, 20, 24, 28, 32,
+                               40, 48, 56, 64, 80, 96};
     std::vector<int> ns;
     for (int n : cand)
         if (n < N && (int)ns.size() < kMaxRules) ns.push_back(n);
