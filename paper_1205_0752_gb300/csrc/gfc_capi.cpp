@@ -222,10 +222,10 @@ static bool tridiag_ql(int n, std::vector<double> &d, std::vector<double> sub,
 static void build_rules(Tables &T, std::vector<double> &r64, std::vector<float4> &r32)
 {
     const int N = (int)T.t.size();
-    // sizes spaced by at most ~25 %, so that the smallest exact rule of a node
+    // sizes spaced by at most ~12 %, so that the smallest exact rule of a node
     // over-provisions little
-    static const int cand[] = {2, 3, 4, 5, 6, 7, 8, 10, 12, 14, 16, 18, 20, 24, 28, 32,
-                               40, 48, 56, 64, 80, 96};
+    static const int cand[] = {2,  3,  4,  5,  6,  7,  8,  9,  10, 11, 12, 13, 14, 16, 18, 20, 22,
+                               24, 27, 30, 33, 36, 40, 44, 48, 53, 58, 64, 70, 77, 85, 96};
     std::vector<int> ns;
     for (int n : cand)
         if (n < N && (int)ns.size() < kMaxRules) ns.push_back(n);

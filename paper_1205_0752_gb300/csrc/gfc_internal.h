@@ -11,7 +11,7 @@ namespace gfc {
 constexpr int kMaxRadial = 16384;
 constexpr int kMaxAngular = 512;
 constexpr int kMaxPairs = kMaxAngular / 2;
-constexpr int kMaxRules = 24;
+constexpr int kMaxRules = 32;
 constexpr int kCounters = 8;   // per-call device counters (see gfc_capi.cpp)
 
 // Contour of one pass of a point (Step 3, eq. 15).
