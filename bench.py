@@ -401,8 +401,9 @@ def run_gfc(args):
         diag[name] = xg.numel() / (a_ev.elapsed_time(b_ev) / 1e3)
 
     # ---- end to end through the host-buffer C-ABI call --------------------
-    import oracle  # grid points of the block, written by the oracle's Kernel 1
-    xh = torch.from_numpy(oracle.grid_points(*rect, side, side)).pin_memory()
+    # the block's grid points, made by the library's own Kernel 1 and held in
+    # pinned host memory before the timed region
+    xh = gfc.grid_points((*rect, side, side), stream=stream).reshape(-1).cpu().pin_memory()
     Gh = torch.empty_like(xh).pin_memory()
     for _ in range(1):
         for p in props:

@@ -2,8 +2,8 @@
 
 ctypes wrapper around ``gfc_oracle.c``: a plain FP64 CPU evaluation of the
 Taylor-subtracted two-point integral (Steps 1-5 of Sect. 2, eqs. 11-15 and 20;
-contours of Sect. 5.3). Only the tests, ``__graft_entry__.smoke()`` and the
-benchmark's CPU-baseline leg may import this package. It imports nothing from
+contours of Sect. 5.3). Only the tests, the smoke check (``smoke()``) and the
+benchmark's CPU-baseline and reference legs may import this package. It imports nothing from
 the product package and the product package imports nothing from it.
 """
 from __future__ import annotations

@@ -18,10 +18,10 @@
  * over points only. Only the test suite, the smoke check and the benchmark's
  * CPU-baseline leg load it; the product library never links or calls it.
  *
- * Readings of points where the paper is silent (all stated in the design doc):
+ * Readings of points where the paper is silent:
  *  - the radial variable is |q| = sqrt(y) on the mapped half-line
  *    |q| = L t/(1-t), t Gauss-Legendre on (0,1) (Lambda^2 -> infinity);
- *  - the angular rule is Gauss-Legendre in psi on [0,pi] with weight
+ *  - the default angular rule is Gauss-Legendre in psi on [0,pi] with weight
  *    sin^(D-2) psi (the paper uses tanh-sinh in z with sqrt(1-z^2));
  *  - the radial ray for complex x runs along arg y = arg x (generalising the
  *    paper's regions 2/5 contour 0 -> 15 e^{i arg x});
