@@ -193,7 +193,10 @@ int gfc_eval_points(const gfc_propagator *prop, const gfc_params *params,
  * factor, (|x| + |y|)/|a| for the angular denominator and, in binary32
  * (GFC_MIXED), |w|/min_j |1 - w t_j| for the angular sum. The rounding error
  * of a point is a small multiple of the unit roundoff of its precision times
- * this number. GFC_F32X2 writes 0 (no scale is computed there). */
+ * this number. Double-float computes no scale and writes 0: all points under
+ * GFC_F32X2, and under GFC_MIXED the points re-evaluated by a GFC_F32X2
+ * fallback (a GFC_FP64 fallback writes its binary64 scale). 0 is also written
+ * where nothing is summed (the cut side, x = mu2). */
 int gfc_eval_points_cond(const gfc_propagator *prop, const gfc_params *params,
                          const double *x, int64_t npts, double *G, double *cond, void *stream);
 

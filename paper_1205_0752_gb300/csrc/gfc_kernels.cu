@@ -36,8 +36,8 @@ g0mu_kernel(const __grid_constant__ KParams kp,
     const PassPre<double, 2> pp2 = pass_pre<double, 2>(kp, P, 0, x);
     const PassPre<double, 1> pp1 = pass_pre<double, 1>(kp, P, 0, x);
     for (int k = warp * 32 + lane; k < nn; k += nwarps * 32) {
-        Node<double> nd = P.clus ? ray_node_cl<double>(kp, k, P.eth, eD, P.cl_c, P.cl_d, P.cl_eta)
-                                 : ray_node<double>(kp, k, P.eth, eD, 0.0);
+        Node<double> nd = P.clus ? ray_node_cl<double>(kp, k, e2, eD, P.cl_c, P.cl_d, P.cl_eta)
+                                 : ray_node<double>(kp, k, e2, eD, 0.0);
         ErrAcc<double> ea = {0.0, 0.0};
         double qm;
         int np;

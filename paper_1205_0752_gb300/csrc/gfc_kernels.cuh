@@ -277,11 +277,18 @@ __device__ __forceinline__ bool in_band(const KParams &kp, double xr, double xi)
 // ----------------------------------------------------------------------------
 // nodes of the contour (Step 3) with the measure (1/2) y^((D-2)/2) dy
 // ----------------------------------------------------------------------------
+// Binary32 and double-float nodes carry their measure divided by (1 + |y|)^2
+// and each of the two propagator fractions times (1 + |y|), so that neither
+// overflows binary32's range far out on the contour; binary64 needs no such
+// scaling and skips its reciprocal.
+template <typename T>
+__host__ __device__ constexpr bool node_scaled() { return !std::is_same<T, double>::value; }
+
 template <typename T>
 struct Node {
     C<T> y;
-    C<T> Jt;    // measure / (1 + |y|)^2
-    T sc;       // 1 + |y|
+    C<T> Jt;    // measure, / (1 + |y|)^2 where node_scaled<T>()
+    T sc;       // 1 + |y| where node_scaled<T>(), else 1
     C<T> ylo;   // binary32 ray nodes: y's rounding remainder (y = y + ylo exactly
                 // for the node |q| = rho_hi + rho_lo on the ray e2); else 0
 };
@@ -318,33 +325,38 @@ __device__ __forceinline__ void load2<float>(const KParams &kp, int which, int k
     b = v.y;
 }
 
-// q-ray node at |q| = rho with weight W: q = rho e^{i theta}, measure
-// q^(D-1) dq
+// q-ray node at |q| = rho with weight W: q = rho e^{i theta}, y = rho^2
+// e^{2 i theta} (e2), measure q^(D-1) dq
 template <typename T>
-__device__ __forceinline__ Node<T> ray_node_at(const KParams &kp, T rho, T W, C<T> eth, C<T> eD)
+__device__ __forceinline__ Node<T> ray_node_at(const KParams &kp, T rho, T W, C<T> e2, C<T> eD)
 {
     Node<T> n;
-    C<T> q = rho * eth;
-    n.y = q * q;
-    T r2 = rho * rho;
-    n.sc = T(1) + r2;
-    T s = rcp(n.sc);
-    s = s * s;
-    // q^(D-1) e^{i theta} = rho^(D-1) e^{i D theta};
-    // rho^(D-1) W / (1 + rho^2)^2, scaled first so binary32 cannot overflow
-    T rs = r2 * s;
-    T mag = (kp.dim == 4 ? rs * rho : rs) * W;
+    const T r2 = rho * rho;
+    n.y = r2 * e2;
+    // q^(D-1) e^{i theta} = rho^(D-1) e^{i D theta}
+    T mag;
+    if constexpr (node_scaled<T>()) {
+        // rho^(D-1) W / (1 + rho^2)^2, scaled first so binary32 cannot overflow
+        n.sc = T(1) + r2;
+        T s = rcp(n.sc);
+        s = s * s;
+        const T rs = r2 * s;
+        mag = (kp.dim == 4 ? rs * rho : rs) * W;
+    } else {
+        n.sc = T(1);
+        mag = (kp.dim == 4 ? r2 * rho : r2) * W;
+    }
     n.Jt = mag * eD;
     return n;
 }
 
 // node k of the mapped ray from |q| = rho0
 template <typename T>
-__device__ __forceinline__ Node<T> ray_node(const KParams &kp, int k, C<T> eth, C<T> eD, T rho0)
+__device__ __forceinline__ Node<T> ray_node(const KParams &kp, int k, C<T> e2, C<T> eD, T rho0)
 {
     T rho, W;
     load2<T>(kp, 0, k, rho, W);
-    Node<T> n = ray_node_at<T>(kp, rho + rho0, W, eth, eD);
+    Node<T> n = ray_node_at<T>(kp, rho + rho0, W, e2, eD);
     n.ylo = {T(0), T(0)};
     return n;
 }
@@ -424,12 +436,12 @@ __device__ __forceinline__ void cl_rho_w(const KParams &kp, int k, double c, dou
 }
 
 template <typename T>
-__device__ __forceinline__ Node<T> ray_node_cl(const KParams &kp, int k, C<T> eth, C<T> eD,
+__device__ __forceinline__ Node<T> ray_node_cl(const KParams &kp, int k, C<T> e2, C<T> eD,
                                                double c, double d, double eta)
 {
     T rho, W;
     cl_rho_w(kp, k, c, d, eta, rho, W);
-    Node<T> n = ray_node_at<T>(kp, rho, W, eth, eD);
+    Node<T> n = ray_node_at<T>(kp, rho, W, e2, eD);
     n.ylo = {T(0), T(0)};
     return n;
 }
@@ -448,10 +460,14 @@ __device__ __forceinline__ Node<T> finish_y_node(const KParams &kp, C<T> y, C<T>
     Node<T> n;
     n.y = y;
     n.ylo = {T(0), T(0)};
-    n.sc = T(1) + tsqrt(cabs2(y));
-    T s = rcp(n.sc);
-    s = s * s;
-    n.Jt = s * (half_pow(kp, y) * dy);
+    n.Jt = half_pow(kp, y) * dy;
+    if constexpr (node_scaled<T>()) {
+        n.sc = T(1) + tsqrt(cabs2(y));
+        T s = rcp(n.sc);
+        n.Jt = (s * s) * n.Jt;
+    } else {
+        n.sc = T(1);
+    }
     return n;
 }
 
@@ -493,11 +509,11 @@ __device__ __forceinline__ DetourPre<T> *detour_slot()
 // detour node k of 3 n_s + n_r: q-segment 0 -> q1, half circle around yp,
 // straight segment out to R_d e^{i phi}, ray to infinity from |q| = sqrt(R_d)
 template <typename T>
-__device__ __forceinline__ Node<T> detour_node(const KParams &kp, int k, C<T> eth, C<T> eD,
+__device__ __forceinline__ Node<T> detour_node(const KParams &kp, int k, C<T> e2, C<T> eD,
                                                const DetourPre<T> &dp)
 {
     const int ns = kp.n_s;
-    if (k >= 3 * ns) return ray_node<T>(kp, k - 3 * ns, eth, eD, dp.sqRd);
+    if (k >= 3 * ns) return ray_node<T>(kp, k - 3 * ns, e2, eD, dp.sqRd);
     T t, w;
     if (k < ns) {
         load2<T>(kp, 1, k, t, w);
@@ -506,12 +522,16 @@ __device__ __forceinline__ Node<T> detour_node(const KParams &kp, int k, C<T> et
         Node<T> n;
         n.y = q * q;
         n.ylo = {T(0), T(0)};
-        n.sc = T(1) + cabs2(q);
-        T s = rcp(n.sc);
-        s = s * s;
         // measure q^(D-1) dq, dq = q1 w
         C<T> qd = kp.dim == 4 ? q * q * q : q * q;
-        n.Jt = s * (w * (qd * q1));
+        n.Jt = w * (qd * q1);
+        if constexpr (node_scaled<T>()) {
+            n.sc = T(1) + cabs2(q);
+            T s = rcp(n.sc);
+            n.Jt = (s * s) * n.Jt;
+        } else {
+            n.sc = T(1);
+        }
         return n;
     }
     if (k < 2 * ns) {
@@ -857,7 +877,9 @@ __device__ __forceinline__ double trsqrt(double x) { return rsqrt(x); }
 __device__ __forceinline__ df trsqrt(df x) { return df(rsqrtf(x.hi), 0.0f); }
 
 // Contribution of one node of one pass: Jt * sum_t c_t P1_t(y)/(y + M2_t) *
-// 2x/a_t * S_t, with the (1 + |y|)^2 scale moved from Jt onto the fractions.
+// 2x/a_t * S_t, with the (1 + |y|)^2 scale (node_scaled) moved from Jt onto
+// the fractions. With FC (one term) the pass's common factor c 2x is left out,
+// for the caller to apply once to the pass's sum.
 // The node's error scale is added to `ea` (binary32, and binary64 with cond
 // output); `qmin` receives the smallest |1 - w t|^2 of its angular sums
 // (binary32).
@@ -866,7 +888,7 @@ __device__ __forceinline__ df trsqrt(df x) { return df(rsqrtf(x.hi), 0.0f); }
 // inputs: |y|/|y + M2| per propagator factor (the contour passes near a pole
 // when arg x is near pi), (|x| + |y|)/|a| for the denominator a, and
 // |w|/|1 - w t|_min for the angular sum next to a pinch (binary32 only).
-template <typename T, int NP, int NT, int V>
+template <typename T, int NP, int NT, int V, int FC = 0>
 __device__ __forceinline__ C<T> node_value(const KParams &kp, const AngTab<T, tab_size<NP>()> &tab,
                                            const T *stab, const void *srules,
                                            const PassPre<T, NT> &pp, C<T> x, const Node<T> &nd,
@@ -878,6 +900,12 @@ __device__ __forceinline__ C<T> node_value(const KParams &kp, const AngTab<T, ta
         if constexpr (f32) return C<T>{(nd.y.r + c.r) + nd.ylo.r, (nd.y.i + c.i) + nd.ylo.i};
         else return nd.y + c;
     };
+    // (1 + |y|)/c where the node is scaled, else 1/c
+    auto sinv = [&](C<T> c) -> C<T> {
+        if constexpr (node_scaled<T>()) return nd.sc * cinv(c);
+        else return cinv(c);
+    };
+    static_assert(!FC || NT == 1, "c 2x is common to the pass only for one term");
     // double-float has no error-scale output (it would cost registers)
     const bool want_mag = std::is_same<T, float>::value ||
                           (std::is_same<T, double>::value && kp.cond_out != nullptr);
@@ -927,17 +955,19 @@ __device__ __forceinline__ C<T> node_value(const KParams &kp, const AngTab<T, ta
         }
         // (1 + |y|)^2 P1(y) / (y + M2)
         const C<T> ypq = ypc(pp.m2q[s]);
-        C<T> pq = nd.sc * cinv(ypq);
+        C<T> pq = sinv(ypq);
         C<T> p1;
         if (pp.same[s]) {
             p1 = pq;
         } else if (pp.full[s]) {
             const C<T> yp = KConst<T>::yp(kp), Rp = KConst<T>::Rp(kp);
-            p1 = nd.sc * (Rp * cinv(ypc(C<T>{-yp.r, -yp.i})) + conj(Rp) * cinv(ypc(C<T>{-yp.r, yp.i})));
+            const C<T> pf = Rp * cinv(ypc(C<T>{-yp.r, -yp.i})) + conj(Rp) * cinv(ypc(C<T>{-yp.r, yp.i}));
+            if constexpr (node_scaled<T>()) p1 = nd.sc * pf;
+            else p1 = pf;
         } else {
-            p1 = nd.sc * cinv(ypc(pp.m2k[s]));
+            p1 = sinv(ypc(pp.m2k[s]));
         }
-        C<T> f = (pp.cx2[s] * (p1 * pq)) * ia[s];
+        C<T> f = FC ? (p1 * pq) * ia[s] : (pp.cx2[s] * (p1 * pq)) * ia[s];
         C<T> fS = f * S;
         sum = sum + fS;
         if (want_mag) {
@@ -952,7 +982,7 @@ __device__ __forceinline__ C<T> node_value(const KParams &kp, const AngTab<T, ta
             } else {
                 kk = ay * rcp(cabs1(nd.y + pp.m2k[s]));
             }
-            const T m = cabs1(fS);
+            const T m = FC ? cabs1(fS) * cabs1(pp.cx2[s]) : cabs1(fS);
             mag += m;
             // with y, y + M2 and a exact to one rounding (binary32 ray nodes)
             // the pole terms weigh less: what remains is the rounding of the
@@ -1053,23 +1083,31 @@ __device__ __forceinline__ void run_pass(const KParams &kp, const AngTab<T, tab_
     }
     // binary32 mapped rays from q = 0 use nodes with y exact (see ray_node_exact_y)
     const bool exact_y = std::is_same<T, float>::value && ray && !(CL && P.clus);
+    // one term (binary64 and double-float): the pass's factor c 2x multiplies
+    // the lane's sum of the pass once instead of every node (binary32 keeps
+    // it per node, where its compensated sum and error scale were set up)
+    constexpr int FC = (NTT == 1 && !std::is_same<T, float>::value) ? 1 : 0;
+    C<T> ps = {T(0), T(0)};
     for (int k = lane; k < nn; k += 32) {
         Node<T> nd;
         if (!ray)
-            nd = detour_node<T>(kp, k, P.eth, eD, *dps);
+            nd = detour_node<T>(kp, k, e2, eD, *dps);
         else if (CL && P.clus)
-            nd = ray_node_cl<T>(kp, k, P.eth, eD, P.cl_c, P.cl_d, P.cl_eta);
+            nd = ray_node_cl<T>(kp, k, e2, eD, P.cl_c, P.cl_d, P.cl_eta);
         else if constexpr (std::is_same<T, float>::value)
             nd = ray_node_exact_y(kp, k, e2, eD);
         else
-            nd = ray_node<T>(kp, k, P.eth, eD, T(0));
+            nd = ray_node<T>(kp, k, e2, eD, T(0));
         T qm;
         int np;
-        C<T> v = node_value<T, NP, NTT, CL>(kp, tab, stab, srules, pp, x, nd, ea, qm, np, exact_y);
-        acc_add(acc, v);
+        C<T> v = node_value<T, NP, NTT, CL, FC>(kp, tab, stab, srules, pp, x, nd, ea, qm, np,
+                                                exact_y);
+        if constexpr (FC) ps = ps + v;
+        else acc_add(acc, v);
         qall = fmin(qall, qm);
         pairs += np;
     }
+    if constexpr (FC) acc_add(acc, pp.cx2[0] * ps);
 }
 
 // Sum over one point's contour, per lane, into acc; returns the point's
