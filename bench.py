@@ -417,6 +417,14 @@ def run_gfc(args):
     e2e_t = max_over_ranks(time.perf_counter() - t0)
     e2e_value = ws * npts_step * e2e_steps / e2e_t
 
+    def decade_hist(e):
+        """counts of relative errors per decade from 1e-15 to 1e-6, plus the
+        open ends below 1e-15 and from 1e-6 up"""
+        edges = [0.0] + [10.0 ** k for k in range(-15, -5)] + [np.inf]
+        counts, _ = np.histogram(e, bins=edges)
+        names = ["<1e-15"] + [f"1e{k}..1e{k + 1}" for k in range(-15, -6)] + [">=1e-6"]
+        return dict(zip(names, (int(v) for v in counts)))
+
     # ---- roofline of the dominant kernel ----------------------------------
     avg_launch_s = float(np.mean(launch_ms)) / 1e3
     achieved = FLOP_PER_NODE_EVAL * node_evals_launch / avg_launch_s / 1e12
@@ -456,12 +464,14 @@ def run_gfc(args):
                   "max_rel_err": float(err.max()), "p99_rel_err": float(np.percentile(err, 99)),
                   "median_rel_err": float(np.median(err)), "max_abs_err": float(abs_err.max()),
                   "frac_rel_err_gt_1e-6": float(np.mean(err > 1e-6)),
+                  "rel_err_hist": decade_hist(err),
                   "fp64_point_fraction": fp64_frac,
                   "error_vs": "FP64 GPU results (parity <= 1e-10 with the oracle)",
                   "fp32_peak_tflops": SM_COUNT * FP32_FMA_PER_SM_CLK * 2 * SM_MAX_MHZ * 1e6 / 1e12,
                   "achieved_tflops": FLOP_PER_NODE_EVAL * 3 * node_evals_launch * args.steps / tmx / 1e12},
         "f32x2": {"value": df_value, "unit": "points/s", "ms_per_step": 1e3 * tdf / args.steps,
                   "max_rel_err": float(err_df.max()), "median_rel_err": float(np.median(err_df)),
+                  "rel_err_hist": decade_hist(err_df),
                   "error_vs": "FP64 GPU results",
                   "arith": "double-float (pairs of binary32) on the binary32 pipes"},
         "mixed_fp64_fallback": {"value": md_value, "unit": "points/s",
