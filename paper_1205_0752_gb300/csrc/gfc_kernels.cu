@@ -37,7 +37,7 @@ g0mu_kernel(const __grid_constant__ KParams kp,
     const PassPre<double, 1> pp1 = pass_pre<double, 1>(kp, P, 0, x);
     for (int k = warp * 32 + lane; k < nn; k += nwarps * 32) {
         Node<double> nd = P.clus ? ray_node_cl<double>(kp, k, e2, eD, P.cl_c, P.cl_d, P.cl_eta)
-                                 : ray_node<double>(kp, k, e2, eD, 0.0);
+                                 : ray_node<double>(kp, k, e2, eD);
         ErrAcc<double> ea = {0.0, 0.0};
         double qm;
         int np;

@@ -350,9 +350,21 @@ __device__ __forceinline__ Node<T> ray_node_at(const KParams &kp, T rho, T W, C<
     return n;
 }
 
-// node k of the mapped ray from |q| = rho0
+// node k of the mapped ray from q = 0
 template <typename T>
-__device__ __forceinline__ Node<T> ray_node(const KParams &kp, int k, C<T> e2, C<T> eD, T rho0)
+__device__ __forceinline__ Node<T> ray_node(const KParams &kp, int k, C<T> e2, C<T> eD)
+{
+    T rho, W;
+    load2<T>(kp, 0, k, rho, W);
+    Node<T> n = ray_node_at<T>(kp, rho, W, e2, eD);
+    n.ylo = {T(0), T(0)};
+    return n;
+}
+
+// node k of the mapped ray from |q| = rho0 > 0 (the tail of a detour)
+template <typename T>
+__device__ __forceinline__ Node<T> ray_node_from(const KParams &kp, int k, C<T> e2, C<T> eD,
+                                                 T rho0)
 {
     T rho, W;
     load2<T>(kp, 0, k, rho, W);
@@ -513,7 +525,7 @@ __device__ __forceinline__ Node<T> detour_node(const KParams &kp, int k, C<T> e2
                                                const DetourPre<T> &dp)
 {
     const int ns = kp.n_s;
-    if (k >= 3 * ns) return ray_node<T>(kp, k - 3 * ns, e2, eD, dp.sqRd);
+    if (k >= 3 * ns) return ray_node_from<T>(kp, k - 3 * ns, e2, eD, dp.sqRd);
     T t, w;
     if (k < ns) {
         load2<T>(kp, 1, k, t, w);
@@ -1097,7 +1109,7 @@ __device__ __forceinline__ void run_pass(const KParams &kp, const AngTab<T, tab_
         else if constexpr (std::is_same<T, float>::value)
             nd = ray_node_exact_y(kp, k, e2, eD);
         else
-            nd = ray_node<T>(kp, k, e2, eD, T(0));
+            nd = ray_node<T>(kp, k, e2, eD);
         T qm;
         int np;
         C<T> v = node_value<T, NP, NTT, CL, FC>(kp, tab, stab, srules, pp, x, nd, ea, qm, np,
