@@ -586,10 +586,12 @@ __device__ __forceinline__ df q_direct(df t, df wr, df wi)
     df di = wi * t;
     return fma(dr, dr, di * di);
 }
-// e r + acc for the positive angular sums A and B (double-float: an add that
-// may assume no cancellation)
-__device__ __forceinline__ float fma_pos(float a, float b, float c) { return fmaf(a, b, c); }
-__device__ __forceinline__ double fma_pos(double a, double b, double c) { return fma(a, b, c); }
+// s += e r for the positive angular sums A and B; double-float accumulates
+// unnormalised (cascaded summation) and pos_finish renormalises once
+__device__ __forceinline__ void pos_acc(float &s, float e, float r) { s = fmaf(e, r, s); }
+__device__ __forceinline__ void pos_acc(double &s, double e, double r) { s = fma(e, r, s); }
+__device__ __forceinline__ float pos_finish(float s) { return s; }
+__device__ __forceinline__ double pos_finish(double s) { return s; }
 
 template <typename T>
 __device__ __forceinline__ T q_horner(T t, T w2, T m2wr)
@@ -701,8 +703,8 @@ __device__ __forceinline__ int pair_sums(const KParams &kp, const AngTab<T, tab_
                 T q = f32 ? q_direct(t, w[s].r, w[s].i) : q_horner(t, w2[s], m2wr[s]);
                 if (f32) qm = fmin(qm, q);
                 T r = rcp(q);
-                A[s] = fma_pos(e, r, A[s]);
-                B[s] = fma_pos(g, r, B[s]);
+                pos_acc(A[s], e, r);
+                pos_acc(B[s], g, r);
             }
         }
     } else if (NP > 0) {
@@ -715,11 +717,11 @@ __device__ __forceinline__ int pair_sums(const KParams &kp, const AngTab<T, tab_
                 if (f32) qm = fmin(qm, q);
                 T r = rcp(q);
                 if (j & 1) {
-                    A1[s] = fma_pos(e, r, A1[s]);
-                    B1[s] = fma_pos(g, r, B1[s]);
+                    pos_acc(A1[s], e, r);
+                    pos_acc(B1[s], g, r);
                 } else {
-                    A[s] = fma_pos(e, r, A[s]);
-                    B[s] = fma_pos(g, r, B[s]);
+                    pos_acc(A[s], e, r);
+                    pos_acc(B[s], g, r);
                 }
             }
         }
@@ -732,15 +734,19 @@ __device__ __forceinline__ int pair_sums(const KParams &kp, const AngTab<T, tab_
                 T q = q_direct(t, w[s].r, w[s].i);
                 if (f32) qm = fmin(qm, q);
                 T r = rcp(q);
-                A[s] = fma_pos(e, r, A[s]);
-                B[s] = fma_pos(g, r, B[s]);
+                pos_acc(A[s], e, r);
+                pos_acc(B[s], g, r);
             }
         }
     }
 #pragma unroll
     for (int s = 0; s < NT; ++s) {
-        A[s] += A1[s];
-        B[s] += B1[s];
+        A[s] = pos_finish(A[s]);
+        B[s] = pos_finish(B[s]);
+        if constexpr (NP > 0) {
+            A[s] += A1[s];
+            B[s] += B1[s];
+        }
     }
     qmin = qm;
     return rule < kp.nrule ? kp.rule_n[rule] : npair;
