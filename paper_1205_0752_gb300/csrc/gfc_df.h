@@ -3,7 +3,7 @@
 // error-free transformations: Knuth's TwoSum, Dekker's FastTwoSum, and the
 // FMA-based TwoProduct (see Ogita, Rump & Oishi, "Accurate sum and dot
 // product", SIAM J. Sci. Comput. 26 (2005)). On a GB300 the binary32 pipes
-// run 64 times the binary64 FMA rate, so these ~10-20 binary32 operations per
+// run 64 times the binary64 FMA rate, so these ~7-11 binary32 operations per
 // double-float operation still outrun native binary64.
 //
 // The exponent range is binary32's (|x| < 3.4e38; the low part underflows
@@ -57,13 +57,15 @@ __device__ __forceinline__ df df_two_prod(float a, float b)
     return df(p, e);
 }
 
+// a + b by Dekker's add: TwoSum of the high parts, the low parts added in
+// binary32. Its error is ~2^-48 (|a| + |b|): relative to a + b it grows with
+// cancellation, as the rounding already carried by computed a and b does; the
+// kernels add no operands that are exact and cancel, so the second TwoSum of
+// the fully accurate add (~20 operations instead of ~11) would buy nothing.
 __device__ __forceinline__ df operator+(df a, df b)
 {
     df s = df_two_sum(a.hi, b.hi);
-    df t = df_two_sum(a.lo, b.lo);
-    s.lo = __fadd_rn(s.lo, t.hi);
-    s = df_fast_two_sum(s.hi, s.lo);
-    s.lo = __fadd_rn(s.lo, t.lo);
+    s.lo = __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo));
     return df_fast_two_sum(s.hi, s.lo);
 }
 
