@@ -40,8 +40,8 @@ MASSES2 = (0.25, 1.0, 4.0)          # m in {0.5, 1, 2}
 NR, NA = 2048, 256
 FLOP_PER_NODE_EVAL = 11              # 22 flops per +-psi pair (9 FMA + 4 MUL)
 # DRAM bytes per point of the FP64 evaluation kernel (ncu, one 256x256 launch of the
-# current kernel: 248,320 B read, 0 B written back before the launch ended)
-TRAFFIC_PER_POINT = 248320 / 65536
+# current kernel: 243,456 B read, 0 B written back before the launch ended)
+TRAFFIC_PER_POINT = 243456 / 65536
 SM_COUNT = 152
 SM_MAX_MHZ = 2070.0
 FP64_FMA_PER_SM_CLK = 2              # nominal GB300 FP64 rate (1.25 TFLOP/s)
@@ -446,7 +446,7 @@ def run_gfc(args):
                      "achieved": achieved, "peak": peak64, "unit": "TFLOP/s",
                      "frac": achieved / peak64, "traffic": TRAFFIC_PER_POINT * side * side,
                      "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one "
-                                       "256x256 launch (248,320 B), scaled by points per launch",
+                                       "256x256 launch (243,456 B), scaled by points per launch",
                      "peak_source": "derived: 152 SM x 2 FP64 FMA/clk x 2 flop x 2070 MHz "
                                     "(ncu: dfma peak_sustained 304/clk = 152 x 2)",
                      "algorithmic": "11 flop per node-eval (22 per +-psi pair)",
