@@ -80,7 +80,18 @@ __device__ __forceinline__ df operator*(df a, df b)
     return df_fast_two_sum(p.hi, p.lo);
 }
 
-__device__ __forceinline__ df fma(df a, df b, df c) { return a * b + c; }
+// a b + c in one pass: the product's high part exactly (FMA TwoProduct) with
+// its low-order terms gathered before Dekker's add, one renormalisation at the
+// end (~15 binary32 operations instead of ~18 for a product, then an add)
+__device__ __forceinline__ df fma(df a, df b, df c)
+{
+    const float p = __fmul_rn(a.hi, b.hi);
+    float pe = __fmaf_rn(a.hi, b.hi, -p);
+    pe = __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, pe));
+    df s = df_two_sum(p, c.hi);
+    s.lo = __fadd_rn(s.lo, __fadd_rn(pe, c.lo));
+    return df_fast_two_sum(s.hi, s.lo);
+}
 
 // Sums of positive products e r without renormalising every term: cascaded
 // summation (Ogita, Rump & Oishi 2005, Sum2, with FMA products). The high
