@@ -62,6 +62,12 @@ __device__ __forceinline__ C<T> operator*(C<T> a, C<T> b)
 {
     return {a.r * b.r - a.i * b.i, a.r * b.i + a.i * b.r};
 }
+// double-float: each component as one product and one fused a b + c
+template <>
+__device__ __forceinline__ C<df> operator*(C<df> a, C<df> b)
+{
+    return {fma(a.r, b.r, -(a.i * b.i)), fma(a.r, b.i, a.i * b.r)};
+}
 template <typename T>
 __device__ __forceinline__ C<T> operator*(T s, C<T> a) { return {s * a.r, s * a.i}; }
 template <typename T>
@@ -117,6 +123,8 @@ __device__ __forceinline__ C<T> csqrt_p(C<T> z)
 
 template <typename T>
 __device__ __forceinline__ T cabs2(C<T> a) { return a.r * a.r + a.i * a.i; }
+template <>
+__device__ __forceinline__ df cabs2(C<df> a) { return fma(a.r, a.r, a.i * a.i); }
 template <typename T>
 __device__ __forceinline__ T cabs1(C<T> a) { return fabs(a.r) + fabs(a.i); }
 
