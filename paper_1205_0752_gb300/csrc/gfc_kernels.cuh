@@ -6,9 +6,11 @@
 //
 // Work layout: one warp per point of x (dynamic assignment through an atomic
 // counter); the 32 lanes split the radial nodes of the point's contour; each
-// lane runs the whole angular sum of its node with the angular table held in
-// the kernel's constant bank (fully unrolled), so the inner loop issues no
-// loads. The angular sum is paired (psi, pi - psi) and written in a
+// lane runs the whole angular sum of its node, over the smallest compressed
+// Gauss rule of the angular measure that is exact to rounding for the node
+// (shared memory, uniform over the warp) or over the full table, held in the
+// kernel's constant bank and fully unrolled. The angular sum is paired
+// (psi, pi - psi) and written in a
 // square-root-free, leading-order-subtracted form:
 //
 //   sum_j w_j (v t_j - 1)/(1 - w t_j)
@@ -20,7 +22,9 @@
 // sum w_j, Omega1 = sum w_j t_j, delta = 4 Omega1 - Omega. This is the
 // combined-fraction integrand of eq. 20 summed over the symmetric pair; each
 // pair costs one real reciprocal and a handful of FMAs, and A, B are sums of
-// positive terms. The radial sum is compensated (TwoSum) in the binary32 path.
+// positive terms. The radial sum is compensated (TwoSum) in the binary32 path,
+// carried in double-float by the double-float kernels and summed plainly in
+// binary64, whose rounding there lies far below the FP64 tolerance.
 #pragma once
 
 #include <math.h>
@@ -998,7 +1002,7 @@ __device__ __forceinline__ C<T> node_value(const KParams &kp, const AngTab<T, ta
             C<T> vw = (v[s] - w[s]) * w[s];
             S = lead + vw * T2;
         }
-        // (1 + |y|)^2 P1(y) / (y + M2)
+        // P1(y) / (y + M2), times (1 + |y|)^2 where the node is scaled
         const C<T> ypq = ypc(pp.m2q[s]);
         C<T> pq = sinv(ypq);
         C<T> p1;
@@ -1067,7 +1071,8 @@ __device__ __forceinline__ void two_sum_add(T &s, T &c, T v)
 }
 
 // binary32: compensated (TwoSum) radial sums; binary64: plain sums (at most
-// n_r/32 terms per lane, error far below the FP64 tolerance)
+// n_r/32 terms per lane, error far below the FP64 tolerance); double-float:
+// sums in double-float
 __device__ __forceinline__ void acc_add(Acc<float> &a, C<float> v)
 {
     two_sum_add(a.sr, a.cr, v.r);
