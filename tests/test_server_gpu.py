@@ -120,3 +120,31 @@ def test_bad_requests_rejected():
             srv.submit({"kind": "scalar", "m2": 1.0}, dict(n_angular=1), (*RECT, 8, 8))
         with pytest.raises(gfc.GfcError):
             srv.submit({"kind": "scalar", "m2": 1.0}, {}, (-2.0, 1.0, -1.5, 1.5, 4, 3))
+
+
+def test_cancel_active_request_between_launches():
+    """A request already on the device stops being scheduled: the launch in
+    flight completes (launches are bounded by the server's work budget, so no
+    kernel polls a flag), no further launch is made for it, its host array is
+    not written, and the server goes on serving."""
+    import time
+    big = dict(dim=4, n_radial=2048, n_angular=256, precision="fp64")
+    with gfc.Server(0, hbm_budget_bytes=1 << 30, max_slots=2) as srv:
+        # 2048 x 2048 points, several launches' worth of work
+        t, G = srv.submit({"kind": "scalar", "m2": 1.0}, big, (*RECT, 2048, 2048))
+        G[:] = 7.0
+        deadline = time.monotonic() + 60.0
+        while srv.request_info(t)["state"] == 0 and time.monotonic() < deadline:
+            time.sleep(0.002)
+        assert srv.request_info(t)["state"] == 1      # on the device, not finished
+        assert srv.cancel(t) == 0
+        assert srv.wait(t, 120000) == -6
+        info = srv.request_info(t)
+        assert info["state"] == 2 and info["status"] == -6
+        assert np.all(G == 7.0)
+        # the server still serves
+        t2, G2 = srv.submit({"kind": "scalar", "m2": 1.0}, dict(big, n_radial=256, n_angular=64),
+                            (*RECT, 16, 16))
+        assert srv.wait(t2, 60000) == 0
+        assert _rel(G2, _alone({"kind": "scalar", "m2": 1.0}, dict(big, n_radial=256, n_angular=64), 16)) <= 1e-10
+        assert srv.stats().canceled == 1
