@@ -38,6 +38,9 @@ RECT = (-10.0, 5.0, -5.0, 5.0)
 SIDE = 1024
 MASSES2 = (0.25, 1.0, 4.0)          # m in {0.5, 1, 2}
 NR, NA = 2048, 256
+# the workload both arms (this library and the oracle) name in their JSON line
+WORKLOAD = ("bubble m in {0.5,1,2}, D=4, mu2=1, 1024x1024 per GPU over [-10,5]x[-5,5], "
+            "2048x256 nodes, FP64")
 FLOP_PER_NODE_EVAL = 11              # 22 flops per +-psi pair (9 FMA + 4 MUL)
 # DRAM bytes per point of the FP64 evaluation kernel (ncu, one 256x256 launch of the
 # current kernel: 243,456 B read, 0 B written back before the launch ended)
@@ -172,8 +175,7 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "impl": "reference",
-            "config": {"workload": "bubble m in {0.5,1,2}, D=4, mu2=1, 1024x1024 per GPU over "
-                                   "[-10,5]x[-5,5], 2048x256 nodes, FP64",
+            "config": {"workload": WORKLOAD,
                        "reference_sample": sample},
             "cpu_baseline": {"value": value, "unit": "points/s", "cores": cores,
                              "kind": "oracle", "sample": sample},
@@ -434,8 +436,7 @@ def run_gfc(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t64 / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": "bubble m in {0.5,1,2}, D=4, mu2=1, 1024x1024 per GPU over "
-                               "[-10,5]x[-5,5], 2048x256 nodes, FP64",
+        "config": {"workload": WORKLOAD,
                    "points_per_step": ws * npts_step, "node_evals_per_step": 3 * node_evals_launch * ws,
                    "l2": "256 MB buffer written before every step (> 129 MB L2)",
                    "parallelism": f"rows sharded over {ws} GPU(s), no collective"},
