@@ -41,7 +41,7 @@ extern "C" {
 #endif
 
 #define GFC_VERSION_MAJOR 1
-#define GFC_VERSION_MINOR 3
+#define GFC_VERSION_MINOR 4
 
 enum {
     GFC_OK = 0,
@@ -256,6 +256,23 @@ int gfc_angular_map(const gfc_propagator *prop, const gfc_params *params, double
  * GFC_ECUDA with the failure in gfc_last_error(); n = 0 clears the hook.
  * GFC_EINVAL for n < 0. */
 int gfc_test_fail_allocations(int n);
+
+/* Test hook (host only, no device work): the angular tables the evaluation
+ * kernels use for n_angular nodes of angular_rule in dimension dim (the
+ * integrand's angular part of eq. 20 summed over the +-psi pairs of a
+ * symmetric rule, Sect. 4). *npair receives the pair count np and, if pairs
+ * is not NULL, pairs[3j .. 3j+2] = (t_j, e_j, g_j) with t_j = cos^2 psi_j,
+ * e_j = w_j t_j^2, g_j = e_j t_j (np <= max_pairs). *nrule receives the
+ * number of compressed rules (at most 32): Gauss rules of the discrete
+ * measure sum_j e_j delta(t - t_j), rule r with rule_n[r] nodes, used by a
+ * binary64 or double-float node whose Bernstein-ellipse parameter of the pole
+ * 1/w is at least rho_min[r]; if rules is not NULL it receives their nodes in
+ * order, 3 doubles (tau, gamma, gamma tau) each (sum of rule_n <=
+ * max_rule_nodes). rule_n and rho_min may be NULL. GFC_EINVAL for parameters
+ * gfc_eval_points would reject, NULL npair or nrule, or short capacity. */
+int gfc_test_angular_rules(int n_angular, int dim, int angular_rule, double *pairs, int max_pairs,
+                           int *npair, double *rules, int max_rule_nodes, int *rule_n,
+                           float *rho_min, int *nrule);
 
 /* gfc_region_map: region 1 of Fig. 2. For each of npts external x (DEVICE
  * complex128), free_out[i] (DEVICE int32) = 1 if the branch cut of B(x, .)

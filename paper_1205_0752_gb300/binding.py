@@ -108,6 +108,9 @@ _SIGS = {
                          ctypes.c_double, _P, ctypes.c_int64, _P, _P], ctypes.c_int),
     "gfc_region_map": ([ctypes.POINTER(_Prop), _P, ctypes.c_int64, _P, _P], ctypes.c_int),
     "gfc_test_fail_allocations": ([ctypes.c_int], ctypes.c_int),
+    "gfc_test_angular_rules": ([ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, ctypes.c_int,
+                                ctypes.POINTER(ctypes.c_int), _P, ctypes.c_int, _P, _P,
+                                ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
 }
 
 _lib = None
@@ -423,3 +426,32 @@ def test_fail_allocations(n: int):
     """Test hook: the next ``n`` device allocations of the library fail
     (gfc_test_fail_allocations); 0 clears it."""
     _check(load_library().gfc_test_fail_allocations(int(n)), "gfc_test_fail_allocations")
+
+
+def angular_rules(n_angular: int, dim: int = 4, angular_rule="gl"):
+    """Test hook (host only): the angular pair table and the compressed rules
+    the kernels use (gfc_test_angular_rules). Returns (pairs, rules, rho_min):
+    pairs an (np, 3) array of (t, e, g), rules a list of (n, 3) arrays of
+    (tau, gamma, gamma tau), rho_min the Bernstein-parameter threshold of each
+    rule (binary64 and double-float)."""
+    import numpy as np
+    lib = load_library()
+    rule = ANGULAR_RULES[angular_rule] if isinstance(angular_rule, str) else int(angular_rule)
+    pairs = np.zeros(3 * 512, dtype=np.float64)
+    rules = np.zeros(3 * 4096, dtype=np.float64)
+    rule_n = np.zeros(32, dtype=np.int32)
+    rho_min = np.zeros(32, dtype=np.float32)
+    npair, nrule = ctypes.c_int(), ctypes.c_int()
+    _check(lib.gfc_test_angular_rules(int(n_angular), int(dim), rule,
+                                      ctypes.c_void_p(pairs.ctypes.data), 512, ctypes.byref(npair),
+                                      ctypes.c_void_p(rules.ctypes.data), 4096,
+                                      ctypes.c_void_p(rule_n.ctypes.data),
+                                      ctypes.c_void_p(rho_min.ctypes.data), ctypes.byref(nrule)),
+           "gfc_test_angular_rules")
+    out, off = [], 0
+    for r in range(nrule.value):
+        n = int(rule_n[r])
+        out.append(rules[3 * off:3 * (off + n)].reshape(n, 3).copy())
+        off += n
+    return (pairs[:3 * npair.value].reshape(-1, 3).copy(), out,
+            rho_min[:nrule.value].astype(np.float64))

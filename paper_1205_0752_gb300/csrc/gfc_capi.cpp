@@ -2,6 +2,7 @@
 // launch sequence of one evaluation (G0(mu2) first, then the points).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <atomic>
 #include <cmath>
 #include <complex>
@@ -414,6 +415,55 @@ static void angular_nodes(int rule, int n, int dim, std::vector<double> &z, std:
     }
 }
 
+// The angular pair table (t_j = cos^2 psi_j, e_j = w_j t_j^2, g_j = e_j t_j)
+// of T's angular rule, its moments Omega, Omega1 and delta, and its compressed
+// rules (host only: the device copies are made by build_tables).
+static void angular_host(Tables &T, std::vector<double> &ang64, std::vector<float> &ang32,
+                         std::vector<double> &r64, std::vector<float4> &r32)
+{
+    // angular pairs: psi_j and pi - psi_j on [0, pi], weight w sin^(D-2) psi;
+    // an odd rule's centre node psi = pi/2 pairs with itself at half weight
+    // (none when the angular integral is taken in closed form)
+    const bool exact = T.ang_rule == GFC_ANG_EXACT;
+    std::vector<double> az(exact ? 0 : T.n_a), aw(exact ? 0 : T.n_a);
+    if (!exact) angular_nodes(T.ang_rule, T.n_a, T.dim, az, aw);
+    int np = exact ? 0 : (T.n_a + 1) / 2;
+    T.t.resize(np);
+    T.e.resize(np);
+    T.g.resize(np);
+    ang64.assign(3 * np, 0.0);
+    ang32.assign(3 * np, 0.0f);
+    double Om = 0, Om1 = 0, c_om = 0, c_om1 = 0;
+    for (int j = 0; j < np; ++j) {
+        const bool centre = 2 * j + 1 == T.n_a;
+        double w = centre ? 0.5 * aw[j] : aw[j];
+        double t = centre ? 0.0 : az[j] * az[j];
+        T.t[j] = t;
+        T.e[j] = w * t * t;
+        T.g[j] = w * t * t * t;
+        ang64[3 * j] = T.t[j];
+        ang64[3 * j + 1] = T.e[j];
+        ang64[3 * j + 2] = T.g[j];
+        ang32[3 * j] = (float)T.t[j];
+        ang32[3 * j + 1] = (float)T.e[j];
+        ang32[3 * j + 2] = (float)T.g[j];
+        // Kahan sums of the pair moments
+        double y = w - c_om, s = Om + y;
+        c_om = (s - Om) - y;
+        Om = s;
+        y = w * t - c_om1;
+        s = Om1 + y;
+        c_om1 = (s - Om1) - y;
+        Om1 = s;
+    }
+    T.Omega = Om;
+    T.Omega1 = Om1;
+    T.delta = 4.0 * Om1 - Om;
+    r64.clear();
+    r32.clear();
+    build_rules(T, r64, r32);
+}
+
 static int build_tables(Tables &T)
 {
     const double pi = 3.14159265358979323846;
@@ -451,47 +501,11 @@ static int build_tables(Tables &T)
         arc64[k] = make_double2(std::cos(pi * t), std::sin(pi * t));
         arc32[k] = make_float2((float)std::cos(pi * t), (float)std::sin(pi * t));
     }
-    // angular pairs: psi_j and pi - psi_j on [0, pi], weight w sin^(D-2) psi;
-    // an odd rule's centre node psi = pi/2 pairs with itself at half weight
-    // (none when the angular integral is taken in closed form)
-    const bool exact = T.ang_rule == GFC_ANG_EXACT;
-    std::vector<double> az(exact ? 0 : T.n_a), aw(exact ? 0 : T.n_a);
-    if (!exact) angular_nodes(T.ang_rule, T.n_a, T.dim, az, aw);
-    int np = exact ? 0 : (T.n_a + 1) / 2;
-    T.t.resize(np);
-    T.e.resize(np);
-    T.g.resize(np);
-    std::vector<double> ang64(3 * np);
-    std::vector<float> ang32(3 * np);
-    double Om = 0, Om1 = 0, c_om = 0, c_om1 = 0;
-    for (int j = 0; j < np; ++j) {
-        const bool centre = 2 * j + 1 == T.n_a;
-        double w = centre ? 0.5 * aw[j] : aw[j];
-        double t = centre ? 0.0 : az[j] * az[j];
-        T.t[j] = t;
-        T.e[j] = w * t * t;
-        T.g[j] = w * t * t * t;
-        ang64[3 * j] = T.t[j];
-        ang64[3 * j + 1] = T.e[j];
-        ang64[3 * j + 2] = T.g[j];
-        ang32[3 * j] = (float)T.t[j];
-        ang32[3 * j + 1] = (float)T.e[j];
-        ang32[3 * j + 2] = (float)T.g[j];
-        // Kahan sums of the pair moments
-        double y = w - c_om, s = Om + y;
-        c_om = (s - Om) - y;
-        Om = s;
-        y = w * t - c_om1;
-        s = Om1 + y;
-        c_om1 = (s - Om1) - y;
-        Om1 = s;
-    }
-    T.Omega = Om;
-    T.Omega1 = Om1;
-    T.delta = 4.0 * Om1 - Om;
-    std::vector<double> r64;
+    std::vector<double> ang64, r64;
+    std::vector<float> ang32;
     std::vector<float4> r32;
-    build_rules(T, r64, r32);
+    angular_host(T, ang64, ang32, r64, r32);
+    const int np = (int)T.t.size();
     // double-float copies (hi = nearest binary32, lo = the rest)
     auto dfv = [](double a) { df v(a); return make_float2(v.hi, v.lo); };
     auto df4 = [](double a, double b) {
@@ -1087,5 +1101,43 @@ extern "C" int gfc_test_fail_allocations(int n)
 {
     if (n < 0) return gfc::fail(GFC_EINVAL, "n must be >= 0");
     gfc::g_fail_allocs.store(n);
+    return GFC_OK;
+}
+
+extern "C" int gfc_test_angular_rules(int n_angular, int dim, int angular_rule, double *pairs,
+                                      int max_pairs, int *npair, double *rules, int max_rule_nodes,
+                                      int *rule_n, float *rho_min, int *nrule)
+{
+    using namespace gfc;
+    if (!npair || !nrule) return fail(GFC_EINVAL, "npair and nrule must not be NULL");
+    gfc_params p;
+    gfc_params_default(&p);
+    p.dim = dim;
+    p.n_angular = n_angular;
+    p.angular_rule = angular_rule;
+    int rc = check_params(&p);
+    if (rc) return rc;
+    Tables T;
+    T.n_r = p.n_radial;
+    T.n_a = n_angular;
+    T.dim = dim;
+    T.ang_rule = angular_rule;
+    T.L = p.radial_scale;
+    std::vector<double> ang64, r64;
+    std::vector<float> ang32;
+    std::vector<float4> r32;
+    angular_host(T, ang64, ang32, r64, r32);
+    const int np = (int)T.t.size();
+    if (pairs && np > max_pairs) return fail(GFC_EINVAL, "pairs: capacity below the pair count");
+    if (rules && T.rules_total > max_rule_nodes)
+        return fail(GFC_EINVAL, "rules: capacity below the rule node count");
+    *npair = np;
+    *nrule = T.nrule;
+    if (pairs) std::copy(ang64.begin(), ang64.end(), pairs);
+    if (rules) std::copy(r64.begin(), r64.end(), rules);
+    for (int r = 0; r < T.nrule; ++r) {
+        if (rule_n) rule_n[r] = T.rule_n[r];
+        if (rho_min) rho_min[r] = T.rho_min64[r];
+    }
     return GFC_OK;
 }
