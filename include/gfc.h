@@ -41,7 +41,7 @@ extern "C" {
 #endif
 
 #define GFC_VERSION_MAJOR 1
-#define GFC_VERSION_MINOR 4
+#define GFC_VERSION_MINOR 5
 
 enum {
     GFC_OK = 0,
@@ -167,6 +167,10 @@ typedef struct {
     int64_t pairs_evaluated;   /* angular +-psi pairs the kernels evaluated; the
                                   compressed angular rules make this smaller
                                   than node_evals / 2 at the same result        */
+    int64_t node_evals_fallback;  /* MIXED: the part of node_evals evaluated by
+                                  the fallback arithmetic; else 0               */
+    int64_t pairs_fallback;    /* MIXED: the part of pairs_evaluated evaluated
+                                  by the fallback arithmetic; else 0            */
 } gfc_eval_stats;
 
 const char *gfc_strerror(int status);
@@ -216,21 +220,23 @@ int gfc_eval_points_host(const gfc_propagator *prop, const gfc_params *params,
                          const double *x_host, int64_t npts, double *G_host, void *stream);
 
 /* gfc_eval_points (GFC_FP64 only) for callers that cannot allocate device
- * memory: code that runs while another component owns the device heap, code
- * that may not call cudaMalloc/cudaFree where it stands (those calls
- * synchronise the device and are not allowed in every context), or an
- * embedding with a fixed device-memory plan. The paper has no counterpart.
+ * memory: code that runs while another component owns the device heap (a
+ * framework's caching allocator, an embedding with a fixed device-memory
+ * plan), or code that must not pay for the device-wide synchronisation that
+ * cudaFree (and often cudaMalloc) implies. The paper has no counterpart.
  * Its node tables and scratch live in one file-scope device array of about
  * 150 KB, so the call allocates nothing (no cudaMalloc, cudaFree or
  * allocating library call); x and G are the caller's DEVICE arrays as for
  * gfc_eval_points. Limits: precision GFC_FP64, n_radial <= 4096, even
  * n_angular <= 512, the Gauss-Legendre angular rule and the mapped radial
- * rule; anything else gives
- * GFC_EINVAL. The array is
- * shared by every call on a device and keeps the last call's contents: calls
- * that overlap on the GPU (other streams or host threads) race on it. The
- * first call on a device looks up the array's address with that device
- * current; make that first call before any stream capture. */
+ * rule, and the full angular table (no compressed rules); anything else
+ * gives GFC_EINVAL. The tables are uploaded from static host arrays of the
+ * library with cudaMemcpyAsync from pageable memory, which may wait for the
+ * work already queued on `stream`. The array is shared by every call on a
+ * device and keeps the last call's contents: calls that overlap on the GPU
+ * (other streams or host threads) race on it. The first call on a device
+ * looks up the array's address with that device current; make that first
+ * call before any stream capture. */
 int gfc_eval_points_noalloc(const gfc_propagator *prop, const gfc_params *params,
                             const double *x, int64_t npts, double *G, void *stream);
 
@@ -256,6 +262,25 @@ int gfc_angular_map(const gfc_propagator *prop, const gfc_params *params, double
  * GFC_ECUDA with the failure in gfc_last_error(); n = 0 clears the hook.
  * GFC_EINVAL for n < 0. */
 int gfc_test_fail_allocations(int n);
+
+/* Test hook (host-side fault injection; the paper has no counterpart): the
+ * next n evaluation-kernel launches (Kernel 2, one-shot or batched by the
+ * server; not the G0(mu2) kernel) report cudaErrorLaunchOutOfResources
+ * without launching anything, so that the error paths of the one-shot calls
+ * and of the serving loop can be exercised without faulting a GPU. A one-shot
+ * call then returns GFC_ECUDA; a served request carried by such a launch
+ * finishes with GFC_ECUDA and its output is not written. n = 0 clears the
+ * hook. GFC_EINVAL for n < 0. */
+int gfc_test_fail_launches(int n);
+
+/* Test switch (the paper has no counterpart): on != 0 makes every later
+ * evaluation sum each radial node's angular integral over the full angular
+ * table instead of the smallest compressed Gauss rule of the table's discrete
+ * measure that reproduces that sum to rounding level; on = 0 restores the
+ * compressed rules. Process-wide; takes effect for calls (and server
+ * admissions) made after it returns. Used to show, at full size, that the
+ * two give the same results. Always GFC_OK. */
+int gfc_test_full_angular_rule(int on);
 
 /* Test hook (host only, no device work): the angular tables the evaluation
  * kernels use for n_angular nodes of angular_rule in dimension dim (the
@@ -288,6 +313,24 @@ int gfc_region_map(const gfc_propagator *prop, const double *x, int64_t npts,
  * work of that call to finish (the counts are read from the device). */
 int gfc_last_stats(gfc_eval_stats *out);
 
+/* Measurement support (the paper has no counterpart): the throughput of the
+ * scalar pipes that bound the evaluation kernels, measured on the current
+ * device. Each rate is thread operations per second of a microkernel that
+ * runs 8 independent dependency chains per thread on SMs x 8 blocks of 256
+ * threads for about `seconds` (best of two timed launches after a
+ * calibration run, CUDA events on `stream`): binary64 FMA (the FP64 pipe),
+ * binary32 FMA (the FMA pipe) and rcp.approx.ftz.f32 (the special-function
+ * unit). These are the denominators of the kernels' executed-work fractions.
+ * Blocks until the probes have finished. GFC_EINVAL for out = NULL or
+ * seconds outside (0, 10]. */
+typedef struct {
+    double dfma_per_s;     /* binary64 fused multiply-adds per second          */
+    double ffma_per_s;     /* binary32 fused multiply-adds per second          */
+    double rcp32_per_s;    /* binary32 approximate reciprocals per second      */
+    int sm_count;          /* multiprocessors of the device                    */
+} gfc_pipe_peaks;
+int gfc_measure_pipe_peaks(gfc_pipe_peaks *out, double seconds, void *stream);
+
 /* Frees the library-owned device memory of the current device (node tables,
  * scratch, staging buffers). Must not overlap any work still running. */
 int gfc_release(void);
@@ -314,9 +357,16 @@ typedef struct {
 int gfc_server_create(int device, size_t hbm_budget_bytes, int max_slots, gfc_server **out);
 
 /* Queues one grid request and returns at once with a ticket. G_host receives
- * m*n complex128 values (host memory that stays valid until the request
- * completes or is cancelled). GFC_EBUDGET if the request alone exceeds the
- * budget, GFC_EINVAL on a bad argument, GFC_EBUSY when shutting down. */
+ * m*n complex128 values, G[i*n + j]; it stays valid until the request
+ * finishes (gfc_server_wait or poll report it done). It is either host memory
+ * (pageable or pinned: the server copies the grid into it through its own
+ * pinned staging once every launch of the request has finished) or device
+ * memory of the server's device (the kernels write it in place, and the
+ * server holds no output buffer for the request). GFC_EBUDGET if the request
+ * alone exceeds the budget, GFC_EINVAL on a bad argument (device memory of
+ * another device included), GFC_EBUSY when shutting down. A request whose
+ * launches or copies hit a CUDA error finishes with GFC_ECUDA and no result
+ * (its host array is not written). */
 int gfc_server_submit(gfc_server *s, const gfc_propagator *prop, const gfc_params *params,
                       const gfc_grid *grid, double *G_host, uint64_t *ticket);
 
@@ -327,8 +377,10 @@ int gfc_server_poll(gfc_server *s, uint64_t ticket, int *done, int *status);
  * status, or GFC_ETIMEOUT if it is still running when the time is up. */
 int gfc_server_wait(gfc_server *s, uint64_t ticket, int timeout_ms);
 
-/* Cancels a request that has not finished; its G_host is not written after
- * this returns GFC_OK. */
+/* Cancels a request that has not finished: no further launch carries its
+ * work. A host G_host is not written after this returns GFC_OK; a device
+ * G_host may still be written by a launch already in flight until
+ * gfc_server_wait reports GFC_ECANCELED. */
 int gfc_server_cancel(gfc_server *s, uint64_t ticket);
 
 int gfc_server_stats(gfc_server *s, gfc_stats *out);

@@ -53,7 +53,8 @@ class _Grid(ctypes.Structure):
 class _EvalStats(ctypes.Structure):
     _fields_ = [("points", ctypes.c_int64), ("points_fp64", ctypes.c_int64),
                 ("node_evals", ctypes.c_int64), ("kernel_launches", ctypes.c_int),
-                ("pairs_evaluated", ctypes.c_int64)]
+                ("pairs_evaluated", ctypes.c_int64), ("node_evals_fallback", ctypes.c_int64),
+                ("pairs_fallback", ctypes.c_int64)]
 
 
 class _ServerStats(ctypes.Structure):
@@ -63,6 +64,11 @@ class _ServerStats(ctypes.Structure):
                 ("points_per_s", ctypes.c_double), ("points_done", ctypes.c_int64),
                 ("bytes_in_use", ctypes.c_size_t), ("bytes_budget", ctypes.c_size_t),
                 ("launches", ctypes.c_int64), ("queued", ctypes.c_int), ("active", ctypes.c_int)]
+
+
+class _PipePeaks(ctypes.Structure):
+    _fields_ = [("dfma_per_s", ctypes.c_double), ("ffma_per_s", ctypes.c_double),
+                ("rcp32_per_s", ctypes.c_double), ("sm_count", ctypes.c_int)]
 
 
 class _RequestInfo(ctypes.Structure):
@@ -108,6 +114,9 @@ _SIGS = {
                          ctypes.c_double, _P, ctypes.c_int64, _P, _P], ctypes.c_int),
     "gfc_region_map": ([ctypes.POINTER(_Prop), _P, ctypes.c_int64, _P, _P], ctypes.c_int),
     "gfc_test_fail_allocations": ([ctypes.c_int], ctypes.c_int),
+    "gfc_test_fail_launches": ([ctypes.c_int], ctypes.c_int),
+    "gfc_measure_pipe_peaks": ([ctypes.POINTER(_PipePeaks), ctypes.c_double, _P], ctypes.c_int),
+    "gfc_test_full_angular_rule": ([ctypes.c_int], ctypes.c_int),
     "gfc_test_angular_rules": ([ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, ctypes.c_int,
                                 ctypes.POINTER(ctypes.c_int), _P, ctypes.c_int, _P, _P,
                                 ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
@@ -290,13 +299,16 @@ class EvalStats:
     node_evals: int
     kernel_launches: int
     pairs_evaluated: int
+    node_evals_fallback: int = 0
+    pairs_fallback: int = 0
 
 
 def last_stats() -> EvalStats:
     lib = load_library()
     s = _EvalStats()
     _check(lib.gfc_last_stats(ctypes.byref(s)), "gfc_last_stats")
-    return EvalStats(s.points, s.points_fp64, s.node_evals, s.kernel_launches, s.pairs_evaluated)
+    return EvalStats(s.points, s.points_fp64, s.node_evals, s.kernel_launches, s.pairs_evaluated,
+                     s.node_evals_fallback, s.pairs_fallback)
 
 
 def version():
@@ -308,6 +320,16 @@ def version():
 
 def release():
     _check(load_library().gfc_release(), "gfc_release")
+
+
+def measure_pipe_peaks(seconds: float = 0.2, stream=None) -> dict:
+    """Measured throughput of the FP64 FMA, FP32 FMA and binary32 reciprocal
+    pipes of the current device (gfc_measure_pipe_peaks), thread ops/s."""
+    p = _PipePeaks()
+    _check(load_library().gfc_measure_pipe_peaks(ctypes.byref(p), float(seconds), _stream_ptr(stream)),
+           "gfc_measure_pipe_peaks")
+    return {"dfma_per_s": p.dfma_per_s, "ffma_per_s": p.ffma_per_s,
+            "rcp32_per_s": p.rcp32_per_s, "sm_count": p.sm_count}
 
 
 # --------------------------------------------------------------------------
@@ -343,14 +365,17 @@ class Server:
         self._keep = {}   # ticket -> host buffer kept alive until completion
 
     def submit(self, prop, params, grid, out=None):
-        """Queues a grid request; returns (ticket, host output array)."""
+        """Queues a grid request; returns (ticket, output array). ``out`` may be
+        a numpy array (host output, the default) or a complex128 CUDA tensor on
+        the server's device (written in place by the kernels)."""
         import numpy as np
         g = grid if isinstance(grid, _Grid) else make_grid(*grid)
         G = out if out is not None else np.empty((g.m, g.n), dtype=np.complex128)
+        ptr = G.ctypes.data if isinstance(G, np.ndarray) else G.data_ptr()
         t = ctypes.c_uint64()
         _check(self._lib.gfc_server_submit(self._h, ctypes.byref(make_prop(prop)),
                                            ctypes.byref(make_params(params)), ctypes.byref(g),
-                                           ctypes.c_void_p(G.ctypes.data), ctypes.byref(t)),
+                                           ctypes.c_void_p(ptr), ctypes.byref(t)),
                "gfc_server_submit")
         self._keep[t.value] = G
         return t.value, G
@@ -426,6 +451,18 @@ def test_fail_allocations(n: int):
     """Test hook: the next ``n`` device allocations of the library fail
     (gfc_test_fail_allocations); 0 clears it."""
     _check(load_library().gfc_test_fail_allocations(int(n)), "gfc_test_fail_allocations")
+
+
+def test_fail_launches(n: int):
+    """Test hook: the next ``n`` evaluation-kernel launches of the library
+    report an error without launching (gfc_test_fail_launches); 0 clears it."""
+    _check(load_library().gfc_test_fail_launches(int(n)), "gfc_test_fail_launches")
+
+
+def test_full_angular_rule(on: bool):
+    """Test switch: the full angular table instead of the compressed rules for
+    every later evaluation (gfc_test_full_angular_rule)."""
+    _check(load_library().gfc_test_full_angular_rule(1 if on else 0), "gfc_test_full_angular_rule")
 
 
 def angular_rules(n_angular: int, dim: int = 4, angular_rule="gl"):

@@ -67,6 +67,24 @@ cudaError_t dev_malloc_async(void **p, size_t bytes, cudaStream_t s)
     return cudaMallocAsync(p, bytes, s);
 }
 
+// test hook: the next g_fail_launches evaluation launches report an error
+// without launching anything
+static std::atomic<int> g_fail_launches{0};
+
+bool take_injected_launch_failure()
+{
+    int v = g_fail_launches.load();
+    while (v > 0 && !g_fail_launches.compare_exchange_weak(v, v - 1)) {
+    }
+    return v > 0;
+}
+
+// test switch: evaluate every node over the full angular table (no
+// compressed rules)
+static std::atomic<int> g_full_rule{0};
+
+bool full_rule_forced() { return g_full_rule.load() != 0; }
+
 // NVTX range for the duration of one ABI call (a no-op without a tool)
 struct NvtxRange {
     explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
@@ -161,61 +179,113 @@ struct Tables {
 // (nodes tau_k, weights gamma_k) integrates polynomials of degree < 2n exactly,
 // so for f(t) = 1/(1 - w t), analytic inside the Bernstein ellipse through the
 // pole t = 1/w, it reproduces T2 with relative error ~ rho^(-2n), rho the
-// ellipse parameter of 2/w - 1. The rule is built by Lanczos on diag(t) from
-// the start vector sqrt(e) (with full reorthogonalisation), and the
-// Golub-Welsch eigenproblem of the resulting Jacobi matrix, solved by the
-// implicit QL method with Wilkinson shifts (Golub & Van Loan, Sect. 8.3).
+// ellipse parameter of 2/w - 1. The recurrence coefficients of mu come from
+// Lanczos on diag(t) with the start vector sqrt(e) (full reorthogonalisation);
+// the rule's nodes are the eigenvalues of the resulting Jacobi matrix and its
+// weights the Christoffel numbers (gauss_from_jacobi).
 // ---------------------------------------------------------------------------
 
-// Implicit QL on the symmetric tridiagonal (d, sub) of order n; on return d
-// holds the eigenvalues and z the first row of the eigenvector matrix.
-static bool tridiag_ql(int n, std::vector<double> &d, std::vector<double> sub,
-                       std::vector<double> &z)
+// Solves T x = r in place for the tridiagonal T (sub-diagonal l[1..n),
+// diagonal d, super-diagonal u[0..n-1)) by Gaussian elimination with partial
+// pivoting (a row swap fills one extra super-diagonal). A zero pivot is
+// replaced by `tiny`: the inverse iteration below solves with a T that is
+// singular to working precision on purpose.
+static void tri_solve(int n, const std::vector<double> &l, const std::vector<double> &d,
+                      const std::vector<double> &u, double tiny, std::vector<double> &r)
 {
-    sub.resize(n, 0.0);
-    z.assign(n, 0.0);
-    z[0] = 1.0;
-    for (int l = 0; l < n; ++l) {
-        int iter = 0, m;
-        do {
-            for (m = l; m < n - 1; ++m) {
-                double dd = std::fabs(d[m]) + std::fabs(d[m + 1]);
-                if (std::fabs(sub[m]) <= 1e-17 * dd) break;
-            }
-            if (m != l) {
-                if (++iter > 80) return false;
-                // Wilkinson shift from the leading 2 x 2 block
-                double g = (d[l + 1] - d[l]) / (2.0 * sub[l]);
-                double r = std::hypot(g, 1.0);
-                g = d[m] - d[l] + sub[l] / (g + (g >= 0 ? r : -r));
-                double s = 1.0, c = 1.0, p = 0.0;
-                int i;
-                for (i = m - 1; i >= l; --i) {
-                    double f = s * sub[i], b = c * sub[i];
-                    r = std::hypot(f, g);
-                    sub[i + 1] = r;
-                    if (r == 0.0) {
-                        d[i + 1] -= p;
-                        sub[m] = 0.0;
-                        break;
-                    }
-                    s = f / r;
-                    c = g / r;
-                    g = d[i + 1] - p;
-                    r = (d[i] - g) * s + 2.0 * c * b;
-                    p = s * r;
-                    d[i + 1] = g + p;
-                    g = c * r - b;
-                    double zf = z[i + 1];
-                    z[i + 1] = s * z[i] + c * zf;
-                    z[i] = c * z[i] - s * zf;
-                }
-                if (r == 0.0 && i >= l) continue;
-                d[l] -= p;
-                sub[l] = g;
-                sub[m] = 0.0;
-            }
-        } while (m != l);
+    std::vector<double> a(n), b(n, 0.0), c(n, 0.0);
+    // the row being eliminated, entries at columns (i, i+1, i+2) and its right side
+    double p0 = d[0], p1 = n > 1 ? u[0] : 0.0, p2 = 0.0, pr = r[0];
+    for (int i = 0; i + 1 < n; ++i) {
+        double q0 = l[i + 1], q1 = d[i + 1], q2 = i + 2 < n ? u[i + 1] : 0.0, qr = r[i + 1];
+        if (std::fabs(q0) > std::fabs(p0)) {
+            std::swap(p0, q0);
+            std::swap(p1, q1);
+            std::swap(p2, q2);
+            std::swap(pr, qr);
+        }
+        if (p0 == 0.0) p0 = tiny;
+        const double m = q0 / p0;
+        a[i] = p0;
+        b[i] = p1;
+        c[i] = p2;
+        r[i] = pr;
+        p0 = q1 - m * p1;
+        p1 = q2 - m * p2;
+        p2 = 0.0;
+        pr = qr - m * pr;
+    }
+    a[n - 1] = p0 == 0.0 ? tiny : p0;
+    r[n - 1] = pr;
+    for (int i = n - 1; i >= 0; --i) {
+        double s = r[i];
+        if (i + 1 < n) s -= b[i] * r[i + 1];
+        if (i + 2 < n) s -= c[i] * r[i + 2];
+        r[i] = s / a[i];
+    }
+}
+
+// Gauss rule of order n from the Jacobi matrix J of a measure of mass mu0
+// (diagonal a[0..n), off-diagonal b[0..n-1), b > 0). Nodes: the eigenvalues
+// of J, each found by bisection on the Sturm count (the number of negative
+// pivots of the LDL^T factorisation of J - lambda I equals the number of
+// eigenvalues below lambda). Weights: mu0 v_0^2 for the unit eigenvector v,
+// found by inverse iteration with the converged eigenvalue (Golub-Welsch).
+// Returns false if a weight is not finite and positive.
+static bool gauss_from_jacobi(int n, const std::vector<double> &a, const std::vector<double> &b,
+                              double mu0, std::vector<double> &nodes, std::vector<double> &weights)
+{
+    // Gershgorin interval holding every eigenvalue
+    double lo = a[0], hi = a[0];
+    for (int i = 0; i < n; ++i) {
+        const double r = (i > 0 ? std::fabs(b[i - 1]) : 0.0) + (i < n - 1 ? std::fabs(b[i]) : 0.0);
+        lo = std::min(lo, a[i] - r);
+        hi = std::max(hi, a[i] + r);
+    }
+    // eigenvalues of J strictly below lam
+    auto count_below = [&](double lam) {
+        int c = 0;
+        double d = 1.0;
+        for (int i = 0; i < n; ++i) {
+            d = (a[i] - lam) - (i > 0 ? b[i - 1] * (b[i - 1] / d) : 0.0);
+            if (d == 0.0) d = -1e-300;   // a zero pivot: perturb lam infinitesimally
+            if (d < 0.0) ++c;
+        }
+        return c;
+    };
+    const double tiny = 1e-30 * std::max(std::fabs(lo), std::fabs(hi));
+    std::vector<double> sub(n, 0.0), dg(n), sup(n, 0.0), v(n);
+    for (int i = 0; i + 1 < n; ++i) {
+        sub[i + 1] = b[i];
+        sup[i] = b[i];
+    }
+    nodes.assign(n, 0.0);
+    weights.assign(n, 0.0);
+    for (int k = 0; k < n; ++k) {
+        // the k-th eigenvalue (ascending) lies where the count passes k
+        double l = lo, h = hi;
+        for (int it = 0; it < 200; ++it) {
+            const double m = 0.5 * (l + h);
+            if (!(m > l && m < h)) break;
+            if (count_below(m) > k) h = m;
+            else l = m;
+        }
+        const double lam = 0.5 * (l + h);
+        nodes[k] = lam;
+        for (int i = 0; i < n; ++i) {
+            dg[i] = a[i] - lam;
+            v[i] = 1.0;
+        }
+        for (int it = 0; it < 3; ++it) {
+            tri_solve(n, sub, dg, sup, tiny, v);
+            double s = 0.0;
+            for (double x : v) s = std::max(s, std::fabs(x));
+            for (double &x : v) x /= s;
+        }
+        double s2 = 0.0;
+        for (double x : v) s2 += x * x;
+        weights[k] = mu0 * v[0] * v[0] / s2;
+        if (!(weights[k] > 0.0) || !std::isfinite(weights[k])) return false;
     }
     return true;
 }
@@ -273,10 +343,8 @@ static void build_rules(Tables &T, std::vector<double> &r64, std::vector<float4>
     const double K64 = 0.5 * std::log(10.0 * std::pow(2.0, 52)), K32 = 0.5 * std::log(10.0 * std::pow(2.0, 26));
     for (int n : ns) {
         if (n > kmax) break;
-        std::vector<double> d(alpha.begin(), alpha.begin() + n), sub(beta.begin(), beta.begin() + n - 1), z;
-        if (!tridiag_ql(n, d, sub, z)) break;
-        std::vector<double> gam(n);
-        for (int k = 0; k < n; ++k) gam[k] = mu0 * z[k] * z[k];
+        std::vector<double> d, gam;
+        if (!gauss_from_jacobi(n, alpha, beta, mu0, d, gam)) break;
         // moment check: exact for t^m, m < 2n
         bool ok = true;
         for (int m = 0; m < 2 * n && ok; ++m) {
@@ -308,8 +376,10 @@ static void build_rules(Tables &T, std::vector<double> &r64, std::vector<float4>
 // Per (device, stream) scratch: calls on one stream are ordered by the
 // stream, so they can share it; calls on different streams get their own.
 // counters: [0] work counter of the first launch, [1] of the second, [2]
-// length of the binary64 list, [3] node-evaluation count, [4] angular pairs
-// evaluated; the G0(mu2) kernel of every call zeroes them.
+// length of the fallback list, [3] node-evaluation count and [4] angular
+// pairs evaluated by the first launch, [5] pairs and [6] node evaluations of
+// the fallback launch (mixed precision); the G0(mu2) kernel of every call
+// zeroes them.
 struct Scratch {
     double *partials = nullptr;   // 2 * kMaxG0Warps
     unsigned *ticket = nullptr;
@@ -710,7 +780,7 @@ static void fill_kparams_tables(KParams &kp, const gfc_params *p, const Tables &
     kp.Omega = T.Omega;
     kp.Omega1 = T.Omega1;
     kp.delta = T.delta;
-    kp.nrule = T.nrule;
+    kp.nrule = full_rule_forced() ? 0 : T.nrule;
     for (int r = 0; r < T.nrule; ++r) {
         kp.rule_off[r] = T.rule_off[r];
         kp.rule_n[r] = T.rule_n[r];
@@ -826,6 +896,9 @@ static int run(const gfc_propagator *prop, const gfc_params *p, KParams kp_point
             if (e != cudaSuccess) return cuda_fail(e, "eval launch (binary32)");
             kp.mode = MODE_LIST64;
             kp.counter = S->counters + 1;
+            // the fallback launch counts its work apart from the binary32 bulk
+            kp.pair_count = S->counters + 5;
+            kp.node_count = S->counters + 6;
             e = launch_eval(kp, tb, p->mixed_fallback == GFC_F32X2 ? ARITH_DF : ARITH_F64, st);
             if (e != cudaSuccess) return cuda_fail(e, "eval launch (binary64 list)");
             stats.kernel_launches += 2;
@@ -1065,8 +1138,10 @@ int gfc_last_stats(gfc_eval_stats *out)
         if (e == cudaSuccess)
             e = cudaMemcpy(c, g_last_call.counters, sizeof c, cudaMemcpyDeviceToHost);
         if (e != cudaSuccess) return cuda_fail(e, "reading the call's counters");
-        out->node_evals = (int64_t)c[3];
-        out->pairs_evaluated = (int64_t)c[4];
+        out->node_evals = (int64_t)(c[3] + c[6]);
+        out->pairs_evaluated = (int64_t)(c[4] + c[5]);
+        out->node_evals_fallback = (int64_t)c[6];
+        out->pairs_fallback = (int64_t)c[5];
         if (g_last_call.precision == GFC_MIXED) out->points_fp64 = (int64_t)c[2];
     }
     return GFC_OK;
@@ -1101,6 +1176,19 @@ extern "C" int gfc_test_fail_allocations(int n)
 {
     if (n < 0) return gfc::fail(GFC_EINVAL, "n must be >= 0");
     gfc::g_fail_allocs.store(n);
+    return GFC_OK;
+}
+
+extern "C" int gfc_test_fail_launches(int n)
+{
+    if (n < 0) return gfc::fail(GFC_EINVAL, "n must be >= 0");
+    gfc::g_fail_launches.store(n);
+    return GFC_OK;
+}
+
+extern "C" int gfc_test_full_angular_rule(int on)
+{
+    gfc::g_full_rule.store(on ? 1 : 0);
     return GFC_OK;
 }
 

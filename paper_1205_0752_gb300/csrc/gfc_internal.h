@@ -168,6 +168,12 @@ int fail(int code, const char *msg);
 // cudaErrorMemoryAllocation without calling the runtime).
 cudaError_t dev_malloc(void **p, size_t bytes);
 cudaError_t dev_malloc_async(void **p, size_t bytes, cudaStream_t s);
+// Test hooks: an evaluation launch (one-shot or batched) that reports
+// cudaErrorLaunchOutOfResources without launching (gfc_test_fail_launches),
+// and the full angular table in place of the compressed rules
+// (gfc_test_full_angular_rule).
+bool take_injected_launch_failure();
+bool full_rule_forced();
 int cuda_fail(cudaError_t e, const char *what);
 int check_params_c(const void *params);
 int check_grid_c(const void *grid);

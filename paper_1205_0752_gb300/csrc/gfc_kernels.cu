@@ -128,6 +128,7 @@ static cudaError_t batch_np(const BatchLaunch &bl, const DevTables &tb, bool two
 cudaError_t launch_batch(const BatchLaunch &bl, const DevTables &tb, int arith, bool two_terms,
                          cudaStream_t st)
 {
+    if (take_injected_launch_failure()) return cudaErrorLaunchOutOfResources;
     if (arith == ARITH_F32) return batch_np<float>(bl, tb, two_terms, st);
     if (arith == ARITH_DF) return batch_np<df>(bl, tb, two_terms, st);
     return batch_np<double>(bl, tb, two_terms, st);
@@ -135,6 +136,7 @@ cudaError_t launch_batch(const BatchLaunch &bl, const DevTables &tb, int arith, 
 
 cudaError_t launch_eval(const KParams &kp, const DevTables &tb, int arith, cudaStream_t st)
 {
+    if (take_injected_launch_failure()) return cudaErrorLaunchOutOfResources;
     if (arith == ARITH_F32) return eval_np<float>(kp, tb, st);
     if (arith == ARITH_DF) return eval_np<df>(kp, tb, st);
     return eval_np<double>(kp, tb, st);

@@ -1381,16 +1381,23 @@ eval_batch_kernel(const KParams *__restrict__ slots, const BatchItem *__restrict
 // ----------------------------------------------------------------------------
 // host launchers
 // ----------------------------------------------------------------------------
+// SM count of the current device, cached per device (devices may differ)
 static inline int sm_count()
 {
-    static int n = 0;
-    if (n == 0) {
-        int dev = 0;
-        cudaGetDevice(&dev);
+    static int cached[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) {
+        int n = 0;
         cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-        if (n <= 0) n = 1;
+        return n > 0 ? n : 1;
     }
-    return n;
+    if (cached[dev] == 0) {
+        int n = 0;
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        cached[dev] = n > 0 ? n : 1;
+    }
+    return cached[dev];
 }
 
 template <typename T, int NP>

@@ -1,14 +1,18 @@
 // gfc_eval_points_noalloc: the binary64 evaluation of gfc_eval_points for
 // callers that cannot allocate device memory -- for example code that runs
-// while another component owns the whole device heap, code that may not call
-// cudaMalloc/cudaFree at that point of its life (they synchronise the device
-// and cannot be issued from inside some callbacks or captured streams), or an
-// embedding with a fixed device-memory plan. Its node tables and scratch live
-// in one file-scope device array of fixed size (kNoAllocBytes), so the call
-// allocates nothing: no cudaMalloc, no cudaFree, no allocating library call.
+// while another component owns the whole device heap (a framework's caching
+// allocator, or an embedding with a fixed device-memory plan), or code that
+// must not pay for the device-wide synchronisation that cudaFree (and often
+// cudaMalloc) implies. Its node tables and scratch live in one file-scope
+// device array of fixed size (kNoAllocBytes), so the call allocates nothing:
+// no cudaMalloc, no cudaFree, no allocating library call.
 //
-// The array is shared by every call in the process on a given device and
-// keeps the contents of the last call; calls that overlap on the GPU (on
+// The tables are built on the host into static arrays of this file and
+// uploaded with cudaMemcpyAsync from that pageable memory; such a copy may
+// wait for the work already queued on the stream before it returns. A mutex
+// serialises the calls of all host threads while the arrays are refilled.
+// The device array is shared by every call in the process on a given device
+// and keeps the contents of the last call; calls that overlap on the GPU (on
 // different streams, or from different host threads) race on it. The first
 // call on a device looks up the array's device address (cudaGetSymbolAddress)
 // with that device current; make that first call before any stream capture.
@@ -226,7 +230,7 @@ extern "C" int gfc_eval_points_noalloc(const gfc_propagator *prop, const gfc_par
                     reinterpret_cast<double *>(base + kOffG0), cnt, st);
     if (e != cudaSuccess) return cuda_fail(e, "g0mu launch");
     if (npts > 0) {
-        e = launch_eval(kp, tb, false, st);
+        e = launch_eval(kp, tb, ARITH_F64, st);
         if (e != cudaSuccess) return cuda_fail(e, "eval launch");
     }
     return GFC_OK;

@@ -25,6 +25,7 @@
 #include <map>
 #include <memory>
 #include <mutex>
+#include <string>
 #include <thread>
 #include <tuple>
 #include <vector>
@@ -64,7 +65,8 @@ struct Request {
     gfc_propagator prop{};
     gfc_params params{};
     gfc_grid grid{};
-    double *G_host = nullptr;
+    double *G_host = nullptr;           // caller's output (host or device)
+    bool G_on_device = false;           // G_host is device memory of the server's device
     int64_t npts = 0;
     size_t bytes = 0;
     ReqState state = R_QUEUED;
@@ -78,6 +80,8 @@ struct Request {
     bool count_pending = false;         // list length being read back
     cudaEvent_t count_done = nullptr;
     bool canceled = false;
+    bool failed = false;                // a CUDA call on its behalf failed
+    std::string fail_msg;
     void *pinned = nullptr;
     size_t pinned_size = 0;
     cudaEvent_t copy_done = nullptr;
@@ -91,6 +95,8 @@ struct Request {
 struct LaunchRec {
     cudaEvent_t done = nullptr;
     bool busy = false;
+    bool failed = false;                // a call issuing the launch failed
+    std::string fail_msg;
     std::vector<std::tuple<Request *, int, int64_t>> reqs;   // request, phase, items
     BatchItem *items_dev = nullptr;
     int64_t *offs_dev = nullptr;
@@ -186,7 +192,7 @@ double work_per_point(const Request &r, int arith)
 
 void release_request(gfc_server *s, Request *r)
 {
-    if (r->G_dev) cudaFreeAsync(r->G_dev, s->admit_stream);
+    if (r->G_dev && !r->G_on_device) cudaFreeAsync(r->G_dev, s->admit_stream);
     r->G_dev = nullptr;
     if (r->list_dev) cudaFreeAsync(r->list_dev, s->admit_stream);
     r->list_dev = nullptr;
@@ -200,6 +206,20 @@ void release_request(gfc_server *s, Request *r)
     r->slot = -1;
     s->bytes_in_use -= r->bytes;
     s->active.erase(std::remove(s->active.begin(), s->active.end(), r), s->active.end());
+}
+
+// Marks a request whose work or copies hit a CUDA error: no further work is
+// scheduled for it, and once nothing of it is in flight it finishes with
+// GFC_ECUDA (its output is never reported as a result).
+void mark_failed(Request *r, const std::string &msg)
+{
+    if (!r->failed) r->fail_msg = msg;
+    r->failed = true;
+}
+
+std::string cuda_msg(const char *what, cudaError_t e)
+{
+    return std::string(what) + ": " + cudaGetErrorName(e);
 }
 
 void finish(gfc_server *s, Request *r, int status)
@@ -230,8 +250,13 @@ int admit(gfc_server *s, Request *r)
     if ((rc = make_prop_c(&r->prop, &r->params, pc))) return rc;
     r->slot = s->free_slots.back();
     s->free_slots.pop_back();
-    cudaError_t e = dev_malloc_async((void **)&r->G_dev, 16 * r->npts, s->admit_stream);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync(request output)");
+    cudaError_t e = cudaSuccess;
+    if (r->G_on_device) {
+        r->G_dev = r->G_host;   // the caller's device array receives the grid directly
+    } else {
+        e = dev_malloc_async((void **)&r->G_dev, 16 * r->npts, s->admit_stream);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync(request output)");
+    }
     const bool mixed = r->params.precision == GFC_MIXED;
     if (mixed) {
         e = dev_malloc_async((void **)&r->list_dev, sizeof(int64_t) * r->npts, s->admit_stream);
@@ -269,7 +294,8 @@ int admit(gfc_server *s, Request *r)
     e = launch_g0mu(kp, tb, r->params.mu2, s->partials_dev, nw, s->ticket_dev,
                     s->g0mu_dev + 2 * r->slot, s->dummy_counters, s->admit_stream);
     if (e != cudaSuccess) return cuda_fail(e, "g0mu launch");
-    cudaEventRecord(s->admit_event, s->admit_stream);
+    e = cudaEventRecord(s->admit_event, s->admit_stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaEventRecord(admission)");
     if (!mixed) {
         int ar = r->params.precision == GFC_F32X2 ? ARITH_DF : ARITH_F64;
         r->phases = {Phase{MODE_ALL, ar, 0, r->npts, 0}};
@@ -296,7 +322,7 @@ void issue_launches(gfc_server *s)
 {
     std::map<GroupKey, std::vector<std::pair<Request *, int>>> groups;
     for (Request *r : s->active) {
-        if (r->canceled) continue;
+        if (r->canceled || r->failed) continue;
         for (int p = 0; p < (int)r->phases.size(); ++p) {
             const Phase &ph = r->phases[p];
             if (ph.end < 0 || ph.next >= ph.end) continue;
@@ -355,12 +381,21 @@ void issue_launches(gfc_server *s)
         }
         cudaStream_t st = s->streams[s->next_stream];
         s->next_stream = (s->next_stream + 1) % kStreams;
-        cudaStreamWaitEvent(st, s->admit_event, 0);
-        cudaMemcpyAsync(L.items_dev, L.items_host, sizeof(BatchItem) * nitems,
-                        cudaMemcpyHostToDevice, st);
-        cudaMemcpyAsync(L.offs_dev, L.offs_host, sizeof(int64_t) * nitems, cudaMemcpyHostToDevice,
-                        st);
-        cudaMemsetAsync(L.counter_dev, 0, sizeof(unsigned long long), st);
+        L.failed = false;
+        L.fail_msg.clear();
+        auto chk = [&L](cudaError_t e, const char *what) {
+            if (e != cudaSuccess && !L.failed) {
+                L.failed = true;
+                L.fail_msg = cuda_msg(what, e);
+            }
+        };
+        chk(cudaStreamWaitEvent(st, s->admit_event, 0), "cudaStreamWaitEvent");
+        chk(cudaMemcpyAsync(L.items_dev, L.items_host, sizeof(BatchItem) * nitems,
+                            cudaMemcpyHostToDevice, st), "cudaMemcpyAsync(items)");
+        chk(cudaMemcpyAsync(L.offs_dev, L.offs_host, sizeof(int64_t) * nitems,
+                            cudaMemcpyHostToDevice, st), "cudaMemcpyAsync(offsets)");
+        chk(cudaMemsetAsync(L.counter_dev, 0, sizeof(unsigned long long), st),
+            "cudaMemsetAsync(counter)");
         BatchLaunch bl;
         bl.slots = s->slots_dev;
         bl.items = L.items_dev;
@@ -375,12 +410,12 @@ void issue_launches(gfc_server *s)
         bl.radial_rule = std::get<6>(key);
         bl.ang_exact = std::get<5>(key) == GFC_ANG_EXACT;
         nvtxRangePushA("gfc_server_launch");
-        cudaError_t e = launch_batch(bl, dev_tables_c(*r0->T), arith, std::get<3>(key) != 0, st);
+        // nothing is launched after a failed copy: the launch would read stale items
+        if (!L.failed) chk(launch_batch(bl, dev_tables_c(*r0->T), arith, std::get<3>(key) != 0, st),
+                           "batched launch");
         nvtxRangePop();
-        if (e != cudaSuccess) {
-            s->error = GFC_ECUDA;
-        }
-        cudaEventRecord(L.done, st);
+        if (L.failed) s->error = GFC_ECUDA;
+        chk(cudaEventRecord(L.done, st), "cudaEventRecord(launch)");
         L.busy = true;
         s->launches++;
     }
@@ -395,9 +430,18 @@ bool progress(gfc_server *s)
         if (!L.busy) continue;
         cudaError_t q = cudaEventQuery(L.done);
         if (q == cudaErrorNotReady) continue;
+        // an error of the launch itself (or of the calls that issued it)
+        // fails every request the launch carried
+        const bool bad = L.failed || q != cudaSuccess;
+        const std::string msg = L.failed ? L.fail_msg : cuda_msg("batched launch", q);
         L.busy = false;
+        L.failed = false;
         changed = true;
-        for (auto &rc : L.reqs) std::get<0>(rc)->phases[std::get<1>(rc)].items_out -= std::get<2>(rc);
+        for (auto &rc : L.reqs) {
+            Request *r = std::get<0>(rc);
+            r->phases[std::get<1>(rc)].items_out -= std::get<2>(rc);
+            if (bad) mark_failed(r, msg);
+        }
         L.reqs.clear();
     }
     std::vector<Request *> act = s->active;
@@ -407,33 +451,52 @@ bool progress(gfc_server *s)
             // mixed: once the binary32 phase is done, read the list length
             Phase &p0 = r->phases[0], &p1 = r->phases[1];
             if (r->count_pending) {
-                if (cudaEventQuery(r->count_done) == cudaSuccess) {
+                const cudaError_t q = cudaEventQuery(r->count_done);
+                if (q == cudaSuccess) {
                     p1.end = (int64_t)s->slot_counts_host[r->slot];
                     r->routed = p1.end;
                     r->count_pending = false;
                     changed = true;
+                } else if (q != cudaErrorNotReady) {
+                    mark_failed(r, cuda_msg("routed-point count", q));
+                    r->count_pending = false;
+                    changed = true;
                 }
-            } else if (!r->canceled && p1.end < 0 && p0.next >= p0.end && p0.items_out == 0) {
-                cudaMemcpyAsync(s->slot_counts_host + r->slot, s->slot_counts_dev + r->slot,
-                                sizeof(unsigned long long), cudaMemcpyDeviceToHost,
-                                s->copy_stream);
-                cudaEventRecord(r->count_done, s->copy_stream);
-                r->count_pending = true;
+            } else if (!r->canceled && !r->failed && p1.end < 0 && p0.next >= p0.end &&
+                       p0.items_out == 0) {
+                cudaError_t e = cudaMemcpyAsync(s->slot_counts_host + r->slot,
+                                                s->slot_counts_dev + r->slot,
+                                                sizeof(unsigned long long),
+                                                cudaMemcpyDeviceToHost, s->copy_stream);
+                if (e == cudaSuccess) e = cudaEventRecord(r->count_done, s->copy_stream);
+                if (e == cudaSuccess) r->count_pending = true;
+                else mark_failed(r, cuda_msg("routed-point count copy", e));
                 changed = true;
             }
         }
         {
             bool idle = true;
             for (const Phase &ph : r->phases) idle = idle && ph.items_out == 0;
-            if (r->canceled && idle && !r->count_pending) {
+            if ((r->canceled || r->failed) && idle && !r->count_pending) {
                 release_request(s, r);
-                finish(s, r, GFC_ECANCELED);
+                if (r->canceled) {
+                    finish(s, r, GFC_ECANCELED);
+                } else {
+                    finish(s, r, GFC_ECUDA);
+                }
                 changed = true;
                 continue;
             }
         }
     copying:
-        if (r->state == R_ACTIVE && !r->canceled && request_complete(r)) {
+        if (r->state == R_ACTIVE && !r->canceled && !r->failed && request_complete(r) &&
+            r->G_on_device) {
+            // the kernels wrote the caller's device array; every launch of the
+            // request has retired, so the result is complete
+            release_request(s, r);
+            finish(s, r, GFC_OK);
+            changed = true;
+        } else if (r->state == R_ACTIVE && !r->canceled && !r->failed && request_complete(r)) {
             r->pinned_size = 16 * r->npts;
             r->pinned = pinned_get(s, r->pinned_size);
             if (!r->pinned || cudaEventCreateWithFlags(&r->copy_done, cudaEventDisableTiming)) {
@@ -441,16 +504,26 @@ bool progress(gfc_server *s)
                 finish(s, r, GFC_ENOMEM);
                 continue;
             }
-            cudaMemcpyAsync(r->pinned, r->G_dev, r->pinned_size, cudaMemcpyDeviceToHost,
-                            s->copy_stream);
-            cudaEventRecord(r->copy_done, s->copy_stream);
+            cudaError_t e = cudaMemcpyAsync(r->pinned, r->G_dev, r->pinned_size,
+                                            cudaMemcpyDeviceToHost, s->copy_stream);
+            if (e == cudaSuccess) e = cudaEventRecord(r->copy_done, s->copy_stream);
+            if (e != cudaSuccess) {
+                release_request(s, r);
+                r->fail_msg = cuda_msg("result copy", e);
+                finish(s, r, GFC_ECUDA);
+                changed = true;
+                continue;
+            }
             r->state = R_COPYING;
             changed = true;
         } else if (r->state == R_COPYING) {
-            if (cudaEventQuery(r->copy_done) == cudaErrorNotReady) continue;
-            if (!r->canceled) std::memcpy(r->G_host, r->pinned, r->pinned_size);
+            const cudaError_t q = cudaEventQuery(r->copy_done);
+            if (q == cudaErrorNotReady) continue;
+            const bool ok = q == cudaSuccess;
+            if (ok && !r->canceled) std::memcpy(r->G_host, r->pinned, r->pinned_size);
             release_request(s, r);
-            finish(s, r, r->canceled ? GFC_ECANCELED : GFC_OK);
+            if (!ok) r->fail_msg = cuda_msg("result copy", q);
+            finish(s, r, r->canceled ? GFC_ECANCELED : (ok ? GFC_OK : GFC_ECUDA));
             changed = true;
         }
     }
@@ -570,7 +643,21 @@ int gfc_server_submit(gfc_server *s, const gfc_propagator *prop, const gfc_param
     r->grid = *grid;
     r->G_host = G_host;
     r->npts = (int64_t)grid->m * grid->n;
-    r->bytes = (params->precision == GFC_MIXED ? 24 : 16) * (size_t)r->npts;
+    {
+        // device memory of the server's device is written in place; anything
+        // else is host memory that receives a copy
+        cudaPointerAttributes a;
+        if (cudaPointerGetAttributes(&a, G_host) == cudaSuccess &&
+            (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged)) {
+            if (a.type == cudaMemoryTypeDevice && a.device != s->device)
+                return fail(GFC_EINVAL, "G is device memory of another device");
+            r->G_on_device = a.type == cudaMemoryTypeDevice;
+        }
+        cudaGetLastError();
+    }
+    // the server holds the output grid (host outputs) and the routed list (mixed)
+    r->bytes = ((r->G_on_device ? 0 : 16) + (params->precision == GFC_MIXED ? 8 : 0)) *
+               (size_t)r->npts;
     r->t_submit = clk::now();
     std::lock_guard<std::mutex> lk(s->mu);
     if (s->stopping) return fail(GFC_EBUSY, "server is shutting down");
@@ -611,6 +698,7 @@ int gfc_server_wait(gfc_server *s, uint64_t ticket, int timeout_ms)
     } else if (!s->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), pred)) {
         return fail(GFC_ETIMEOUT, "request still running");
     }
+    if (r->status == GFC_ECUDA && !r->fail_msg.empty()) fail(GFC_ECUDA, r->fail_msg.c_str());
     return r->status;
 }
 

@@ -30,7 +30,7 @@ def test_every_declared_function_is_exported():
 
 
 def test_version_and_strings():
-    assert gfc.version() == (1, 4)
+    assert gfc.version() == (1, 5)
     lib = gfc.load_library()
     assert lib.gfc_strerror(0) == b"ok"
     assert lib.gfc_strerror(-3) == b"request exceeds the memory budget"

@@ -59,12 +59,22 @@ def _cases():
             out.append((3, f"dressed draw {k} (a={a:.3f}, b={b:.3f}, c={c:.3f}) D={dim}, 48 of 512^2, 1024x128",
                         {"kind": "dressed", "a": a, "b": b, "c": c},
                         dict(dim=dim, mu2=1.0, n_radial=1024, n_angular=128), xd[idx]))
-    # points of the production grid within 0.05 of the cut x <= -4 (m = 1)
-    d = np.where(xp.real <= -4.0, np.abs(xp.imag), np.abs(xp - (-4.0)))
-    band = np.flatnonzero(d < 0.05)
-    pick = band[si.sample_indices(90, band.size, 256)]
-    out.append((4, f"production m^2=1, 256 of its {band.size} points within 0.05 of the cut",
-                {"kind": "scalar", "m2": 1.0}, dict(dim=4, mu2=1.0, n_radial=2048, n_angular=256), xp[pick]))
+    # for every mass: points of the production grid within 0.05 of the cut
+    # x <= -4 m^2, and the near-axis strip below threshold (|Im x| < 0.5,
+    # -4 m^2 < Re x < 0), where the sums cancel most
+    for k, m2 in enumerate((0.25, 1.0, 4.0)):
+        thr = -4.0 * m2
+        d = np.where(xp.real <= thr, np.abs(xp.imag), np.abs(xp - thr))
+        band = np.flatnonzero(d < 0.05)
+        pick = band[si.sample_indices(90 + k, band.size, 128)]
+        out.append((4, f"production m^2={m2}, 128 of its {band.size} points within 0.05 of the cut",
+                    {"kind": "scalar", "m2": m2}, dict(dim=4, mu2=1.0, n_radial=2048, n_angular=256),
+                    xp[pick]))
+        strip = np.flatnonzero((np.abs(xp.imag) < 0.5) & (xp.real > thr) & (xp.real < 0.0))
+        pick = strip[si.sample_indices(95 + k, strip.size, 128)]
+        out.append((4, f"production m^2={m2}, 128 of its {strip.size} near-axis points below threshold",
+                    {"kind": "scalar", "m2": m2}, dict(dim=4, mu2=1.0, n_radial=2048, n_angular=256),
+                    xp[pick]))
     return out
 
 

@@ -70,6 +70,49 @@ def test_injected_allocation_failure_in_the_server():
 def test_hook_rejects_negative_counts():
     with pytest.raises(gfc.GfcError):
         binding.test_fail_allocations(-1)
+    with pytest.raises(gfc.GfcError):
+        binding.test_fail_launches(-1)
+
+
+def test_injected_launch_failure_one_shot():
+    par = dict(dim=4, mu2=1.0, n_radial=256, n_angular=64, precision="fp64")
+    xt = torch.tensor(X, device="cuda")
+    binding.test_fail_launches(1)
+    try:
+        with pytest.raises(gfc.GfcError) as e:
+            gfc.eval_points(SCALAR, par, xt)
+        assert e.value.status == GFC_ECUDA
+    finally:
+        binding.test_fail_launches(0)
+    G = gfc.eval_points(SCALAR, par, xt)
+    torch.cuda.synchronize()
+    ref = _oracle(par)
+    assert np.max(np.abs(G.cpu().numpy() - ref) / np.abs(ref)) < 1e-10
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_injected_launch_failure_in_the_server_is_not_a_result(precision):
+    """A batched launch that fails finishes every request it carried with
+    GFC_ECUDA, and the host array is not written; later requests succeed."""
+    rect = si.grid_rect("small")
+    par = dict(dim=4, mu2=1.0, n_radial=256, n_angular=64, precision=precision)
+    with gfc.Server(0, hbm_budget_bytes=64 << 20, max_slots=4) as srv:
+        sentinel = np.full((16, 16), 7.0 + 7.0j)
+        binding.test_fail_launches(1)
+        try:
+            t, G = srv.submit(SCALAR, par, (*rect, 16, 16), out=sentinel)
+            assert srv.wait(t, 60000) == GFC_ECUDA
+            assert b"launch" in gfc.load_library().gfc_last_error()
+            assert srv.request_info(t)["status"] == GFC_ECUDA
+            assert np.all(G == 7.0 + 7.0j)
+        finally:
+            binding.test_fail_launches(0)
+        t, G = srv.submit(SCALAR, par, (*rect, 16, 16))
+        assert srv.wait(t, 60000) == 0
+        assert srv.stats().completed == 1
+    alone = gfc.eval_grid(SCALAR, par, (*rect, 16, 16)).cpu().numpy()
+    tol = 1e-6 if precision == "mixed" else 1e-10
+    assert np.max(np.abs(G - alone) / np.abs(alone)) < tol
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed", "f32x2"])

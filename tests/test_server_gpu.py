@@ -148,3 +148,25 @@ def test_cancel_active_request_between_launches():
         assert srv.wait(t2, 60000) == 0
         assert _rel(G2, _alone({"kind": "scalar", "m2": 1.0}, dict(big, n_radial=256, n_angular=64), 16)) <= 1e-10
         assert srv.stats().canceled == 1
+
+
+def test_device_output_equals_host_output():
+    """G may be device memory of the server's device: the kernels write it in
+    place (no output buffer counted against the budget) and the result equals
+    the host-output request's and the one-shot call's."""
+    mix = _mix()[:4]
+    with gfc.Server(0, hbm_budget_bytes=8 << 20, max_slots=3) as srv:
+        host = [srv.submit(p, q, (*RECT, s, s)) for p, q, s in mix]
+        dev = [srv.submit(p, q, (*RECT, s, s),
+                          out=torch.empty((s, s), dtype=torch.complex128, device="cuda"))
+               for p, q, s in mix]
+        for (t, _), (td, _) in zip(host, dev):
+            assert srv.wait(t, 120000) == 0
+            assert srv.wait(td, 120000) == 0
+        for (td, _), (p, q, s) in zip(dev, mix):
+            info = srv.request_info(td)
+            assert info["bytes"] == (8 * s * s if q["precision"] == "mixed" else 0)
+    for (_, Gh), (_, Gd), (p, q, s) in zip(host, dev, mix):
+        gd = Gd.cpu().numpy()
+        assert np.array_equal(gd, Gh)
+        assert _rel(gd, _alone(p, q, s)) <= RTOL[q["precision"]]

@@ -54,6 +54,35 @@ def test_two_calls_match_the_allocating_entry_point():
         assert _rel(got, ref.cpu().numpy()) <= RTOL
 
 
+def test_makes_no_device_allocation():
+    """With the library's allocation hook armed (its next device allocation
+    would fail) the call still succeeds, and the device's free memory is the
+    same before and after a warmed-up call."""
+    from paper_1205_0752_gb300 import binding
+    g = si.SplitMix64(22)
+    xs = np.array([complex(-8 + 12 * g.uniform(), -4 + 8 * g.uniform()) for _ in range(64)])
+    xt = torch.tensor(xs, dtype=torch.complex128, device="cuda")
+    prop, par = {"kind": "scalar", "m2": 1.0}, dict(dim=4, mu2=1.0, n_radial=256, n_angular=64)
+    ref = gfc.eval_points(prop, dict(par, precision="fp64"), xt).cpu().numpy()
+    lib = gfc.load_library()
+    G = torch.empty_like(xt)
+    args = (ctypes.byref(gfc.make_prop(prop)), ctypes.byref(gfc.make_params(par)),
+            ctypes.c_void_p(xt.data_ptr()), xt.numel(), ctypes.c_void_p(G.data_ptr()))
+    binding.test_fail_allocations(1)
+    try:
+        for _ in range(2):
+            torch.cuda.synchronize()
+            free0 = torch.cuda.mem_get_info()[0]
+            assert lib.gfc_eval_points_noalloc(*args, None) == 0, lib.gfc_last_error()
+            torch.cuda.synchronize()
+            free1 = torch.cuda.mem_get_info()[0]
+    finally:
+        binding.test_fail_allocations(0)
+    # the second call ran with every kernel loaded: nothing was allocated
+    assert free1 == free0
+    assert _rel(G.cpu().numpy(), ref) <= RTOL
+
+
 def test_rejects_sizes_beyond_its_limits():
     lib = gfc.load_library()
     xt = torch.tensor([1 + 1j], dtype=torch.complex128, device="cuda")
