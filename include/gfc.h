@@ -171,6 +171,10 @@ typedef struct {
                                   the fallback arithmetic; else 0               */
     int64_t pairs_fallback;    /* MIXED: the part of pairs_evaluated evaluated
                                   by the fallback arithmetic; else 0            */
+    int64_t pairs_full_table;  /* the part of pairs_evaluated summed over the
+                                  full angular table (nodes next to a pinch,
+                                  where no compressed rule is exact)            */
+    int64_t pairs_full_table_fallback;  /* MIXED: the fallback's part of it     */
 } gfc_eval_stats;
 
 const char *gfc_strerror(int status);
@@ -316,15 +320,18 @@ int gfc_last_stats(gfc_eval_stats *out);
 /* Measurement support (the paper has no counterpart): the throughput of the
  * scalar pipes that bound the evaluation kernels, measured on the current
  * device. Each rate is thread operations per second of a microkernel that
- * runs 8 independent dependency chains per thread on SMs x 8 blocks of 256
- * threads for about `seconds` (best of two timed launches after a
- * calibration run, CUDA events on `stream`): binary64 FMA (the FP64 pipe),
- * binary32 FMA (the FMA pipe) and rcp.approx.ftz.f32 (the special-function
- * unit). These are the denominators of the kernels' executed-work fractions.
- * Blocks until the probes have finished. GFC_EINVAL for out = NULL or
+ * runs 8 or 16 independent dependency chains per thread on SMs x 4 or 8
+ * blocks of 256 threads (the best of these configurations, each the best of
+ * two timed launches of about seconds/4 after a calibration run, CUDA events
+ * on `stream`): binary64 FMA, multiply and add (the FP64 pipe), binary32 FMA
+ * (the FMA pipe) and rcp.approx.ftz.f32 (the special-function unit). These
+ * are the denominators of the kernels' executed-work fractions. Blocks until
+ * the probes have finished (about 10 x seconds). GFC_EINVAL for out = NULL or
  * seconds outside (0, 10]. */
 typedef struct {
     double dfma_per_s;     /* binary64 fused multiply-adds per second          */
+    double dmul_per_s;     /* binary64 multiplies per second                   */
+    double dadd_per_s;     /* binary64 adds per second                         */
     double ffma_per_s;     /* binary32 fused multiply-adds per second          */
     double rcp32_per_s;    /* binary32 approximate reciprocals per second      */
     int sm_count;          /* multiprocessors of the device                    */

@@ -54,7 +54,8 @@ class _EvalStats(ctypes.Structure):
     _fields_ = [("points", ctypes.c_int64), ("points_fp64", ctypes.c_int64),
                 ("node_evals", ctypes.c_int64), ("kernel_launches", ctypes.c_int),
                 ("pairs_evaluated", ctypes.c_int64), ("node_evals_fallback", ctypes.c_int64),
-                ("pairs_fallback", ctypes.c_int64)]
+                ("pairs_fallback", ctypes.c_int64), ("pairs_full_table", ctypes.c_int64),
+                ("pairs_full_table_fallback", ctypes.c_int64)]
 
 
 class _ServerStats(ctypes.Structure):
@@ -67,7 +68,8 @@ class _ServerStats(ctypes.Structure):
 
 
 class _PipePeaks(ctypes.Structure):
-    _fields_ = [("dfma_per_s", ctypes.c_double), ("ffma_per_s", ctypes.c_double),
+    _fields_ = [("dfma_per_s", ctypes.c_double), ("dmul_per_s", ctypes.c_double),
+                ("dadd_per_s", ctypes.c_double), ("ffma_per_s", ctypes.c_double),
                 ("rcp32_per_s", ctypes.c_double), ("sm_count", ctypes.c_int)]
 
 
@@ -301,6 +303,8 @@ class EvalStats:
     pairs_evaluated: int
     node_evals_fallback: int = 0
     pairs_fallback: int = 0
+    pairs_full_table: int = 0
+    pairs_full_table_fallback: int = 0
 
 
 def last_stats() -> EvalStats:
@@ -308,7 +312,8 @@ def last_stats() -> EvalStats:
     s = _EvalStats()
     _check(lib.gfc_last_stats(ctypes.byref(s)), "gfc_last_stats")
     return EvalStats(s.points, s.points_fp64, s.node_evals, s.kernel_launches, s.pairs_evaluated,
-                     s.node_evals_fallback, s.pairs_fallback)
+                     s.node_evals_fallback, s.pairs_fallback, s.pairs_full_table,
+                     s.pairs_full_table_fallback)
 
 
 def version():
@@ -328,8 +333,8 @@ def measure_pipe_peaks(seconds: float = 0.2, stream=None) -> dict:
     p = _PipePeaks()
     _check(load_library().gfc_measure_pipe_peaks(ctypes.byref(p), float(seconds), _stream_ptr(stream)),
            "gfc_measure_pipe_peaks")
-    return {"dfma_per_s": p.dfma_per_s, "ffma_per_s": p.ffma_per_s,
-            "rcp32_per_s": p.rcp32_per_s, "sm_count": p.sm_count}
+    return {"dfma_per_s": p.dfma_per_s, "dmul_per_s": p.dmul_per_s, "dadd_per_s": p.dadd_per_s,
+            "ffma_per_s": p.ffma_per_s, "rcp32_per_s": p.rcp32_per_s, "sm_count": p.sm_count}
 
 
 # --------------------------------------------------------------------------

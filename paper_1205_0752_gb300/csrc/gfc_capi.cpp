@@ -378,8 +378,9 @@ static void build_rules(Tables &T, std::vector<double> &r64, std::vector<float4>
 // counters: [0] work counter of the first launch, [1] of the second, [2]
 // length of the fallback list, [3] node-evaluation count and [4] angular
 // pairs evaluated by the first launch, [5] pairs and [6] node evaluations of
-// the fallback launch (mixed precision); the G0(mu2) kernel of every call
-// zeroes them.
+// the fallback launch (mixed precision), [7] and [8] the pairs of the first
+// and the fallback launch that were the full table's; the G0(mu2) kernel of
+// every call zeroes them.
 struct Scratch {
     double *partials = nullptr;   // 2 * kMaxG0Warps
     unsigned *ticket = nullptr;
@@ -816,6 +817,7 @@ static void fill_kparams(KParams &kp, const gfc_params *p, const Tables &T, cons
     kp.list_count = S.counters + 2;
     kp.node_count = S.counters + 3;
     kp.pair_count = S.counters + 4;
+    kp.pair_full_count = S.counters + 7;
 }
 
 static int grow_list(Scratch &S, int64_t n)
@@ -899,6 +901,7 @@ static int run(const gfc_propagator *prop, const gfc_params *p, KParams kp_point
             // the fallback launch counts its work apart from the binary32 bulk
             kp.pair_count = S->counters + 5;
             kp.node_count = S->counters + 6;
+            kp.pair_full_count = S->counters + 8;
             e = launch_eval(kp, tb, p->mixed_fallback == GFC_F32X2 ? ARITH_DF : ARITH_F64, st);
             if (e != cudaSuccess) return cuda_fail(e, "eval launch (binary64 list)");
             stats.kernel_launches += 2;
@@ -1142,6 +1145,8 @@ int gfc_last_stats(gfc_eval_stats *out)
         out->pairs_evaluated = (int64_t)(c[4] + c[5]);
         out->node_evals_fallback = (int64_t)c[6];
         out->pairs_fallback = (int64_t)c[5];
+        out->pairs_full_table = (int64_t)(c[7] + c[8]);
+        out->pairs_full_table_fallback = (int64_t)c[8];
         if (g_last_call.precision == GFC_MIXED) out->points_fp64 = (int64_t)c[2];
     }
     return GFC_OK;

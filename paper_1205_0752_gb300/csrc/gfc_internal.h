@@ -12,7 +12,7 @@ constexpr int kMaxRadial = 16384;
 constexpr int kMaxAngular = 512;
 constexpr int kMaxPairs = kMaxAngular / 2;
 constexpr int kMaxRules = 32;
-constexpr int kCounters = 8;   // per-call device counters (see gfc_capi.cpp)
+constexpr int kCounters = 12;  // per-call device counters (see gfc_capi.cpp)
 
 // Contour of one pass of a point (Step 3, eq. 15).
 enum PassKind : int { PASS_RAY = 0, PASS_DETOUR = 1 };
@@ -103,6 +103,7 @@ struct KParams {
     unsigned long long *counter;  // work counter for dynamic point assignment
     unsigned long long *node_count;  // optional: contour nodes x angular nodes
     unsigned long long *pair_count;  // optional: angular pairs actually evaluated
+    unsigned long long *pair_full_count;  // optional: the part of them over the full table
 };
 
 // Angular pair table: t = cos^2 psi_j, e = w t^2, g = w t^3 (w includes the

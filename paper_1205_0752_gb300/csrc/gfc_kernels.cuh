@@ -780,7 +780,8 @@ __device__ __forceinline__ int pair_sums(const KParams &kp, const AngTab<T, tab_
         }
     }
     qmin = qm;
-    return rule < kp.nrule ? kp.rule_n[rule] : npair;
+    // pairs evaluated; negative when they were the full table's
+    return rule < kp.nrule ? kp.rule_n[rule] : -npair;
 }
 
 // The angular integral in closed form, the limit of every angular rule: half
@@ -931,7 +932,8 @@ __device__ __forceinline__ df trsqrt(df x) { return df(rsqrtf(x.hi), 0.0f); }
 // for the caller to apply once to the pass's sum.
 // The node's error scale is added to `ea` (binary32, and binary64 with cond
 // output); `qmin` receives the smallest |1 - w t|^2 of its angular sums
-// (binary32).
+// (binary32); `npairs` the angular pairs evaluated, negated when they were
+// the full table's.
 //
 // kappa_k, the relative sensitivity of the node's value to rounding of its
 // inputs: |y|/|y + M2| per propagator factor (the contour passes near a pole
@@ -1120,7 +1122,7 @@ template <typename T, int NP, int NTT, int CL>
 __device__ __forceinline__ void run_pass(const KParams &kp, const AngTab<T, tab_size<NP>()> &tab,
                                          const T *stab, const void *srules, const Plan<T> &P,
                                          int pass, C<T> x, C<T> e2, C<T> eD, int lane, Acc<T> &acc,
-                                         ErrAcc<T> &ea, T &qall, int &pairs)
+                                         ErrAcc<T> &ea, T &qall, int &pairs, int &pfull)
 {
     const PassPre<T, NTT> pp = pass_pre<T, NTT>(kp, P, pass, x);
     const bool ray = P.kind[pass] == PASS_RAY;
@@ -1155,7 +1157,12 @@ __device__ __forceinline__ void run_pass(const KParams &kp, const AngTab<T, tab_
         if constexpr (FC) ps = ps + v;
         else acc_add(acc, v);
         qall = fmin(qall, qm);
-        pairs += np;
+        if (np < 0) {
+            pfull -= np;
+            pairs -= np;
+        } else {
+            pairs += np;
+        }
     }
     if constexpr (FC) acc_add(acc, pp.cx2[0] * ps);
 }
@@ -1166,7 +1173,7 @@ template <typename T, int NP, int NT, int CL>
 __device__ __forceinline__ int point_sum(const KParams &kp, const AngTab<T, tab_size<NP>()> &tab,
                                          const T *stab, const void *srules, double xr, double xi,
                                          int lane, Acc<T> &acc, ErrAcc<T> &ea, T &qall,
-                                         int &pairs)
+                                         int &pairs, int &pfull)
 {
     const Plan<T> P = make_plan<T, CL>(kp, xr, xi);
     const C<T> x = cvt<T>(xr, xi);
@@ -1180,10 +1187,10 @@ __device__ __forceinline__ int point_sum(const KParams &kp, const AngTab<T, tab_
         total += P.kind[pass] == PASS_RAY ? kp.n_r : 3 * kp.n_s + kp.n_r;
         if (NT > 1 && P.nterm[pass] == 2)
             run_pass<T, NP, (NT > 1 ? 2 : 1), CL>(kp, tab, stab, srules, P, pass, x, e2, eD, lane,
-                                                 acc, ea, qall, pairs);
+                                                 acc, ea, qall, pairs, pfull);
         else
             run_pass<T, NP, 1, CL>(kp, tab, stab, srules, P, pass, x, e2, eD, lane, acc, ea, qall,
-                                   pairs);
+                                   pairs, pfull);
     }
     return total;
 }
@@ -1223,15 +1230,22 @@ __device__ __forceinline__ void eval_point(const KParams &kp, const AngTab<T, ta
     acc.init();
     ErrAcc<T> ea = {T(0), T(0)};
     T qall = T(1e30);
-    int pairs = 0;
-    int nodes = point_sum<T, NP, NT, CL>(kp, tab, stab, srules, xr, xi, lane, acc, ea, qall, pairs);
+    int pairs = 0, pfull = 0;
+    int nodes = point_sum<T, NP, NT, CL>(kp, tab, stab, srules, xr, xi, lane, acc, ea, qall, pairs,
+                                         pfull);
     if (kp.node_count && lane == 0)
         atomicAdd(kp.node_count, (unsigned long long)nodes * (unsigned long long)(2 * kp.npair));
     if (kp.pair_count) {
-        unsigned long long pw = (unsigned long long)pairs;
+        unsigned long long pw = (unsigned long long)pairs, pf = (unsigned long long)pfull;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) pw += __shfl_xor_sync(0xffffffffu, pw, o);
-        if (lane == 0) atomicAdd(kp.pair_count, pw);
+        for (int o = 16; o > 0; o >>= 1) {
+            pw += __shfl_xor_sync(0xffffffffu, pw, o);
+            pf += __shfl_xor_sync(0xffffffffu, pf, o);
+        }
+        if (lane == 0) {
+            atomicAdd(kp.pair_count, pw);
+            if (kp.pair_full_count) atomicAdd(kp.pair_full_count, pf);
+        }
     }
     double sr, si, cond;
     if constexpr (std::is_same<T, float>::value) {

@@ -1,10 +1,10 @@
 // gfc_measure_pipe_peaks: throughput of the scalar pipes that bound the
-// evaluation kernels (binary64 FMA, binary32 FMA, the binary32 reciprocal of
-// the special-function unit), measured on the current device. Each probe
-// kernel runs ILP independent dependency chains per thread on a grid of SMs x
-// 8 blocks of 256 threads, long enough (about `seconds`) for the clocks to
-// settle; the rate is the number of thread operations over the CUDA-event
-// time. These are the denominators of the kernels' executed-work fractions.
+// evaluation kernels (binary64 FMA, multiply and add, binary32 FMA, the
+// binary32 reciprocal of the special-function unit), measured on the current
+// device. Each probe kernel runs 8 or 16 independent dependency chains per
+// thread on SMs x 4 or 8 blocks of 256 threads; the rate is the number of
+// thread operations over the CUDA-event time of the best configuration.
+// These are the denominators of the kernels' executed-work fractions.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -15,74 +15,77 @@
 namespace gfc {
 namespace {
 
-constexpr int kIlp = 8;
 constexpr int kUnroll = 4;   // chain steps per loop iteration
 constexpr int kThreads = 256;
-constexpr int kBlocksPerSm = 8;
 
-__global__ void __launch_bounds__(kThreads) probe_dfma(int iters, double b, double c, double *sink)
+// OP: 0 binary64 FMA, 1 binary64 multiply, 2 binary64 add, 3 binary32 FMA,
+// 4 binary32 approximate reciprocal; ILP independent chains per thread
+template <int OP, int ILP>
+__global__ void __launch_bounds__(kThreads) probe_kernel(int iters, double b, double c, double *sink)
 {
-    double a[kIlp];
+    if constexpr (OP <= 2) {
+        double a[ILP];
 #pragma unroll
-    for (int j = 0; j < kIlp; ++j) a[j] = 1e-3 * threadIdx.x + j;
-    for (int i = 0; i < iters; ++i) {
+        for (int j = 0; j < ILP; ++j) a[j] = 1.0 + 1e-3 * threadIdx.x + j;
+        for (int i = 0; i < iters; ++i) {
 #pragma unroll
-        for (int u = 0; u < kUnroll; ++u)
+            for (int u = 0; u < kUnroll; ++u)
 #pragma unroll
-            for (int j = 0; j < kIlp; ++j) a[j] = fma(a[j], b, c);
+                for (int j = 0; j < ILP; ++j) {
+                    if constexpr (OP == 0) a[j] = fma(a[j], b, c);
+                    else if constexpr (OP == 1) a[j] = a[j] * b;
+                    else a[j] = a[j] + c;
+                }
+        }
+        double s = 0.0;
+#pragma unroll
+        for (int j = 0; j < ILP; ++j) s += a[j];
+        if (s == -1.0) sink[0] = s;   // never true for these inputs; keeps the chains live
+    } else {
+        const float bf = (float)b, cf = (float)c;
+        float a[ILP];
+#pragma unroll
+        for (int j = 0; j < ILP; ++j) a[j] = 1.0f + 1e-3f * threadIdx.x + j;
+        for (int i = 0; i < iters; ++i) {
+#pragma unroll
+            for (int u = 0; u < kUnroll; ++u)
+#pragma unroll
+                for (int j = 0; j < ILP; ++j) {
+                    if constexpr (OP == 3) a[j] = fmaf(a[j], bf, cf);
+                    else asm volatile("rcp.approx.ftz.f32 %0, %1;" : "=f"(a[j]) : "f"(a[j]));
+                }
+        }
+        float s = 0.0f;
+#pragma unroll
+        for (int j = 0; j < ILP; ++j) s += a[j];
+        if (s == -1.0f) sink[0] = s;
     }
-    double s = 0.0;
-#pragma unroll
-    for (int j = 0; j < kIlp; ++j) s += a[j];
-    if (s == -1.0) sink[0] = s;   // never true for these inputs; keeps the chains live
 }
 
-__global__ void __launch_bounds__(kThreads) probe_ffma(int iters, float b, float c, float *sink)
+template <int OP>
+cudaError_t launch_probe(int ilp, int blocks, int iters, double *sink, cudaStream_t st)
 {
-    float a[kIlp];
-#pragma unroll
-    for (int j = 0; j < kIlp; ++j) a[j] = 1e-3f * threadIdx.x + j;
-    for (int i = 0; i < iters; ++i) {
-#pragma unroll
-        for (int u = 0; u < kUnroll; ++u)
-#pragma unroll
-            for (int j = 0; j < kIlp; ++j) a[j] = fmaf(a[j], b, c);
-    }
-    float s = 0.0f;
-#pragma unroll
-    for (int j = 0; j < kIlp; ++j) s += a[j];
-    if (s == -1.0f) sink[0] = s;
+    // multiply and FMA chains converge (b < 1); add chains grow slowly
+    const double b = OP == 3 ? 0.999 : 0.9999999, c = OP == 3 ? 1e-3 : 1e-9;
+    if (ilp == 8) probe_kernel<OP, 8><<<blocks, kThreads, 0, st>>>(iters, b, c, sink);
+    else probe_kernel<OP, 16><<<blocks, kThreads, 0, st>>>(iters, b, c, sink);
+    return cudaGetLastError();
 }
 
-__global__ void __launch_bounds__(kThreads) probe_rcp32(int iters, float *sink)
-{
-    float a[kIlp];
-#pragma unroll
-    for (int j = 0; j < kIlp; ++j) a[j] = 1.0f + 1e-3f * threadIdx.x + j;
-    for (int i = 0; i < iters; ++i) {
-#pragma unroll
-        for (int u = 0; u < kUnroll; ++u)
-#pragma unroll
-            for (int j = 0; j < kIlp; ++j) asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(a[j]) : "f"(a[j]));
-    }
-    float s = 0.0f;
-#pragma unroll
-    for (int j = 0; j < kIlp; ++j) s += a[j];
-    if (s == -1.0f) sink[0] = s;
-}
-
-// thread operations per launch of `iters` iterations
-double ops_of(int blocks, int iters) { return (double)blocks * kThreads * iters * kUnroll * kIlp; }
-
-// seconds of one launch of probe `which` with `iters` iterations, or < 0
-double time_probe(int which, int blocks, int iters, double *dsink, cudaStream_t st,
+// seconds of one launch of probe `op` with `iters` iterations, or < 0
+double time_probe(int op, int ilp, int blocks, int iters, double *sink, cudaStream_t st,
                   cudaEvent_t e0, cudaEvent_t e1)
 {
     if (cudaEventRecord(e0, st) != cudaSuccess) return -1.0;
-    if (which == 0) probe_dfma<<<blocks, kThreads, 0, st>>>(iters, 0.999999, 1e-6, dsink);
-    else if (which == 1) probe_ffma<<<blocks, kThreads, 0, st>>>(iters, 0.999f, 1e-3f, (float *)dsink);
-    else probe_rcp32<<<blocks, kThreads, 0, st>>>(iters, (float *)dsink);
-    if (cudaGetLastError() != cudaSuccess) return -1.0;
+    cudaError_t e;
+    switch (op) {
+    case 0: e = launch_probe<0>(ilp, blocks, iters, sink, st); break;
+    case 1: e = launch_probe<1>(ilp, blocks, iters, sink, st); break;
+    case 2: e = launch_probe<2>(ilp, blocks, iters, sink, st); break;
+    case 3: e = launch_probe<3>(ilp, blocks, iters, sink, st); break;
+    default: e = launch_probe<4>(ilp, blocks, iters, sink, st); break;
+    }
+    if (e != cudaSuccess) return -1.0;
     if (cudaEventRecord(e1, st) != cudaSuccess) return -1.0;
     if (cudaEventSynchronize(e1) != cudaSuccess) return -1.0;
     float ms = 0.0f;
@@ -113,31 +116,37 @@ extern "C" int gfc_measure_pipe_peaks(gfc_pipe_peaks *out, double seconds, void 
         if (e0) cudaEventDestroy(e0);
         return cuda_fail(e, "cudaEventCreate");
     }
-    const int blocks = sms * kBlocksPerSm;
-    double rate[3] = {0.0, 0.0, 0.0};
+    // every probe at 8 and 16 chains per thread and 4 and 8 blocks per SM;
+    // the best configuration gives the pipe's rate
+    double rate[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
     int rc = GFC_OK;
-    for (int which = 0; which < 3 && rc == GFC_OK; ++which) {
-        // calibrate the iteration count to about `seconds` per launch, then
-        // keep the best of two timed launches
-        int iters = 64;
-        double t = time_probe(which, blocks, iters, sink, st, e0, e1);
-        for (int k = 0; k < 20 && t >= 0.0 && t < 0.05 * seconds && iters < (1 << 24); ++k) {
-            iters *= 4;
-            t = time_probe(which, blocks, iters, sink, st, e0, e1);
-        }
-        if (t < 0.0) {
-            rc = fail(GFC_ECUDA, "probe launch failed");
-            break;
-        }
-        const double scale = std::min(seconds / std::max(t, 1e-6), 2e9 / iters);
-        iters = (int)std::max(1.0, iters * scale);
-        for (int k = 0; k < 2; ++k) {
-            t = time_probe(which, blocks, iters, sink, st, e0, e1);
-            if (t <= 0.0) {
+    for (int op = 0; op < 5 && rc == GFC_OK; ++op) {
+        for (int cfg = 0; cfg < 4 && rc == GFC_OK; ++cfg) {
+            const int ilp = cfg & 1 ? 16 : 8, blocks = sms * (cfg & 2 ? 8 : 4);
+            const double per = seconds / 4.0;
+            // calibrate the iteration count to about `per` per launch, then
+            // keep the best of two timed launches
+            int iters = 16;
+            double t = time_probe(op, ilp, blocks, iters, sink, st, e0, e1);
+            for (int k = 0; k < 20 && t >= 0.0 && t < 0.05 * per && iters < (1 << 24); ++k) {
+                iters *= 4;
+                t = time_probe(op, ilp, blocks, iters, sink, st, e0, e1);
+            }
+            if (t < 0.0) {
                 rc = fail(GFC_ECUDA, "probe launch failed");
                 break;
             }
-            rate[which] = std::max(rate[which], ops_of(blocks, iters) / t);
+            const double scale = std::min(per / std::max(t, 1e-6), 2e9 / iters);
+            iters = (int)std::max(1.0, iters * scale);
+            for (int k = 0; k < 2; ++k) {
+                t = time_probe(op, ilp, blocks, iters, sink, st, e0, e1);
+                if (t <= 0.0) {
+                    rc = fail(GFC_ECUDA, "probe launch failed");
+                    break;
+                }
+                const double ops = (double)blocks * kThreads * iters * kUnroll * ilp;
+                rate[op] = std::max(rate[op], ops / t);
+            }
         }
     }
     cudaEventDestroy(e0);
@@ -145,8 +154,10 @@ extern "C" int gfc_measure_pipe_peaks(gfc_pipe_peaks *out, double seconds, void 
     cudaFree(sink);
     if (rc != GFC_OK) return rc;
     out->dfma_per_s = rate[0];
-    out->ffma_per_s = rate[1];
-    out->rcp32_per_s = rate[2];
+    out->dmul_per_s = rate[1];
+    out->dadd_per_s = rate[2];
+    out->ffma_per_s = rate[3];
+    out->rcp32_per_s = rate[4];
     out->sm_count = sms;
     return GFC_OK;
 }

@@ -66,10 +66,11 @@ def _cases():
         thr = -4.0 * m2
         d = np.where(xp.real <= thr, np.abs(xp.imag), np.abs(xp - thr))
         band = np.flatnonzero(d < 0.05)
-        pick = band[si.sample_indices(90 + k, band.size, 128)]
-        out.append((4, f"production m^2={m2}, 128 of its {band.size} points within 0.05 of the cut",
-                    {"kind": "scalar", "m2": m2}, dict(dim=4, mu2=1.0, n_radial=2048, n_angular=256),
-                    xp[pick]))
+        if band.size:     # (the cut of m = 2 starts at -16, outside the grid)
+            pick = band[si.sample_indices(90 + k, band.size, min(128, band.size))]
+            out.append((4, f"production m^2={m2}, {pick.size} of its {band.size} points within 0.05 "
+                           f"of the cut", {"kind": "scalar", "m2": m2},
+                        dict(dim=4, mu2=1.0, n_radial=2048, n_angular=256), xp[pick]))
         strip = np.flatnonzero((np.abs(xp.imag) < 0.5) & (xp.real > thr) & (xp.real < 0.0))
         pick = strip[si.sample_indices(95 + k, strip.size, 128)]
         out.append((4, f"production m^2={m2}, 128 of its {strip.size} near-axis points below threshold",

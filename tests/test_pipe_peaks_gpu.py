@@ -17,7 +17,7 @@ def test_pipe_peaks_are_measured_and_repeatable():
     b = gfc.measure_pipe_peaks(0.05)
     sms = torch.cuda.get_device_properties(0).multi_processor_count
     assert a["sm_count"] == sms
-    for k in ("dfma_per_s", "ffma_per_s", "rcp32_per_s"):
+    for k in ("dfma_per_s", "dmul_per_s", "dadd_per_s", "ffma_per_s", "rcp32_per_s"):
         assert a[k] > 1e10, (k, a[k])
         assert abs(a[k] - b[k]) <= 0.15 * max(a[k], b[k]), (k, a[k], b[k])
     assert a["ffma_per_s"] > 8 * a["dfma_per_s"]
