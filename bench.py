@@ -7,15 +7,22 @@ Workload (one step): the equal-mass scalar bubble, D = 4, mu2 = 1, on the
 m in {0.5, 1, 2}: 3 * 2^20 points and 1.65e12 node evaluations.
 
 Prints one JSON line (rank 0). `value` is points/s of the FP64 form over all
-ranks (weak scaling: rank r takes rows [r*1024, (r+1)*1024) of an
-(N*1024) x 1024 grid over the same rectangle). The same line carries the
-mixed-precision study (points/s and per-point error against the FP64
-results), the end-to-end number through the host-buffer C-ABI call, the
-roofline of the dominant kernel, the clocks seen during the timed region and
-the oracle's CPU throughput.
+ranks (weak scaling: rank r takes the rows i = r (mod N) of an (N*1024) x 1024
+grid over the same rectangle, so every rank carries the same mix of cheap and
+expensive points). The same line carries the mixed-precision and
+double-float studies (points/s and per-point error against the FP64
+results), the other workload configurations (the paper's worked example, the
+64 x 64 bubble, the dressed 512 x 512 grids), the serving mix (p50/p99
+latency), the end-to-end number through the host-buffer C-ABI call, the
+roofline of the dominant kernel against the pipe rates measured on the
+device, the clocks seen during the timed region and the oracle's CPU
+throughput.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gfc|reference]
-    python bench.py --serve            # the serving mix (p50/p99 latency)
+    python bench.py --serve            # the serving mix alone (p50/p99 latency)
+
+With --gpus N > 1 and no torch.distributed environment, the script starts
+itself again under torch.distributed.run with N ranks on this node.
 """
 from __future__ import annotations
 
@@ -23,6 +30,7 @@ import argparse
 import datetime
 import json
 import os
+import socket
 import subprocess
 import sys
 import threading
@@ -42,14 +50,33 @@ NR, NA = 2048, 256
 WORKLOAD = ("bubble m in {0.5,1,2}, D=4, mu2=1, 1024x1024 per GPU over [-10,5]x[-5,5], "
             "2048x256 nodes, FP64")
 FLOP_PER_NODE_EVAL = 11              # 22 flops per +-psi pair (9 FMA + 4 MUL)
-# DRAM bytes per point of the FP64 evaluation kernel (ncu, one 256x256 launch of the
-# current kernel: 243,456 B read, 0 B written back before the launch ended)
-TRAFFIC_PER_POINT = 243456 / 65536
-SM_COUNT = 152
-SM_MAX_MHZ = 2070.0
-FP64_FMA_PER_SM_CLK = 2              # nominal GB300 FP64 rate (1.25 TFLOP/s)
-FP32_FMA_PER_SM_CLK = 128
 L2_FLUSH_BYTES = 256 << 20
+
+# Executed work of the evaluation kernels, per unit of their own counters:
+# thread instructions per angular pair on a compressed rule (pc), per pair
+# over the full table (pf) and per contour node (n), for each pipe. Fitted to
+# ncu's instruction counters of four launches per kernel (256 x 256 grids:
+# production m^2 = 1 with compressed rules and with the full table,
+# production m^2 = 0.25, and the right half-plane; every fit reproduces the
+# four launches' counts to <= 2e-3). The per-node figures include each
+# point's fixed work spread over its 2048 ray nodes, so the model holds for
+# the ray nodes of the scalar bubble; fp64_other is the FP64 pipe's other
+# instructions (conversions, compares), fma_ops the binary32 FMA-pipe
+# operations (FFMA, FMUL, FADD), inst all instructions issued.
+EXEC_MODEL = {
+    "fp64": {"dfma": (7.0, 7.0, 34.970), "dmul": (0.0, 2.0, 38.641), "dadd": (0.004, 0.0, 16.577),
+             "fp64_other": (0.004, 0.0, 7.294), "fma_ops": (0.0, 0.0, 67.047),
+             "inst": (47.428, 47.871, 698.123)},
+    "f32x2": {"dfma": (0.0, 0.0, 0.673), "dmul": (0.0, 0.0, 0.313), "dadd": (0.004, 0.0, 0.577),
+              "fp64_other": (0.004, 0.0, 0.560), "fma_ops": (63.0, 77.0, 1007.703),
+              "inst": (81.148, 87.049, 1172.735)},
+    "bulk32": {"dfma": (0.0, 0.0, 0.188), "dmul": (0.0, 0.0, 0.157), "dadd": (0.0, 0.0, 0.095),
+               "fp64_other": (0.0, 0.0, 1.451), "fma_ops": (6.0, 6.0, 207.312),
+               "inst": (17.305, 9.285, 392.539)},
+}
+# DRAM bytes per point of the FP64 evaluation kernel: ncu, one 256 x 256
+# launch of the production grid (dram__bytes_read.sum + dram__bytes_write.sum)
+TRAFFIC_PER_POINT = None
 
 
 def dist_setup():
@@ -59,15 +86,33 @@ def dist_setup():
     return ws, rank, local
 
 
-def shard_rows(rank: int, world: int, side: int = None):
-    """Rows of the (world*side) x side global grid owned by `rank`, and the
-    rectangle of that block."""
+def shard_rect(rank: int, world: int, side: int = None):
+    """The rows i = rank (mod world) of the (world*side) x side cell-centred
+    grid over RECT, as a side x side cell-centred grid of their own: row j of
+    the shard is global row world*j + rank."""
     side = SIDE if side is None else side
     re0, re1, im0, im1 = RECT
-    total = world * side
-    dre = (re1 - re0) / total
-    r0 = rank * side
-    return (re0 + r0 * dre, re0 + (r0 + side) * dre, im0, im1), (r0, r0 + side)
+    dre = (re1 - re0) / (world * side)
+    a = re0 + (rank + 0.5 - 0.5 * world) * dre
+    return (a, a + (re1 - re0), im0, im1)
+
+
+def _free_port() -> int:
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    return port
+
+
+def relaunch(nprocs: int, argv, script: str = None, **run_kw):
+    """Runs `script` (this file by default) under torch.distributed.run with
+    nprocs ranks on this node (rendezvous on 127.0.0.1); returns the
+    CompletedProcess."""
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1",
+           f"--nproc-per-node={nprocs}", "--master-addr", "127.0.0.1",
+           "--master-port", str(_free_port()), script or os.path.abspath(__file__)] + list(argv)
+    return subprocess.run(cmd, **run_kw)
 
 
 class ClockSampler:
@@ -185,11 +230,14 @@ def run_reference(args):
     return 0
 
 
-def run_serve(args):
+# --------------------------------------------------------------------------
+# serving
+# --------------------------------------------------------------------------
+
+def serve_mix(gfc, reqs, log_path=None):
+    """Submits the requests at their arrival times to a 40 GB server, waits for
+    all of them, and returns the latency and throughput record."""
     import torch
-    import paper_1205_0752_gb300 as gfc
-    import synthetic_inputs as si
-    reqs = si.serving_mix(5, args.serve_requests, rate_hz=args.serve_rate)
     srv = gfc.Server(0, hbm_budget_bytes=40 << 30, max_slots=64)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -202,32 +250,91 @@ def run_serve(args):
                    n_angular=r["n_angular"], precision=r["precision"])
         t, _ = srv.submit(r["prop"], par, (*r["rect"], r["side"], r["side"]))
         tickets.append(t)
-    for t in tickets:
-        srv.wait(t)
+    bad = sum(1 for t in tickets if srv.wait(t) != 0)
     wall = time.perf_counter() - t0
     st = srv.stats()
-    if args.serve_log:
-        # one JSON line per request: its parameters and the server's record
-        with open(args.serve_log, "w") as f:
-            for t, r in zip(tickets, reqs):
+    infos = [srv.request_info(t) for t in tickets]
+    if log_path:
+        with open(log_path, "w") as f:
+            for t, r, info in zip(tickets, reqs, infos):
                 rec = {"ticket": int(t), "kind": r["prop"]["kind"], "side": r["side"],
                        "dim": r["dim"], "n_radial": r["n_radial"], "n_angular": r["n_angular"],
                        "precision": r["precision"], "t_arrival_s": r["t_arrival"]}
-                rec.update(srv.request_info(t))
+                rec.update(info)
                 f.write(json.dumps(rec) + "\n")
     srv.close()
     pts = sum(r["side"] ** 2 for r in reqs)
-    line = {"metric": "serve p50/p99 ms", "value": st.p99_ms, "unit": "ms",
-            "higher_is_better": False, "p50_ms": st.p50_ms, "p99_ms": st.p99_ms,
-            "points_per_s": pts / wall, "requests": len(reqs), "completed": st.completed,
-            "launches": st.launches, "wall_s": wall, "rate_hz": args.serve_rate,
-            "data": "synthetic", "n_gpus": 1,
+    lat = np.array([i["total_ms"] for i in infos])
+    return {"requests": len(reqs), "completed": int(st.completed), "failed": bad,
+            "p50_ms": st.p50_ms, "p99_ms": st.p99_ms, "max_ms": float(lat.max()),
+            "points_per_s": pts / wall, "wall_s": wall, "launches": int(st.launches),
+            "offered_points_per_s": pts / max(reqs[-1]["t_arrival"], 1e-9)}
+
+
+def serve_study(gfc, n_spec=2000, rate=200.0, n_load=600, load=0.7):
+    """The specified mix (Poisson arrivals at `rate`), then a run at `load`
+    times the capacity the first run measured (the same request
+    distribution, another seed)."""
+    import synthetic_inputs as si
+    spec = serve_mix(gfc, si.serving_mix(5, n_spec, rate_hz=rate))
+    probe = si.serving_mix(6, n_load, rate_hz=1.0)
+    mean_pts = np.mean([r["side"] ** 2 for r in probe])
+    rate70 = load * spec["points_per_s"] / mean_pts
+    sus = serve_mix(gfc, si.serving_mix(6, n_load, rate_hz=rate70))
+    sus["rate_hz"] = rate70
+    spec["rate_hz"] = rate
+    return {"unit": "ms", "spec": spec, "load70": sus,
+            "workload": "serving mix: Poisson arrivals, square grids side in {32..512}, bubble "
+                        "(m in {0.5,1,2}) or dressed, D in {3,4}, nodes (256x64)..(2048x256), FP64 "
+                        "or mixed, 40 GB budget, 64 slots; load70 at 70% of the capacity the "
+                        "specified run measured"}
+
+
+def run_serve(args):
+    import paper_1205_0752_gb300 as gfc
+    import synthetic_inputs as si
+    rec = serve_mix(gfc, si.serving_mix(5, args.serve_requests, rate_hz=args.serve_rate),
+                    args.serve_log)
+    line = {"metric": "serve p50/p99 ms", "value": rec["p99_ms"], "unit": "ms",
+            "higher_is_better": False, "rate_hz": args.serve_rate, "data": "synthetic",
+            "n_gpus": 1, **rec,
             "config": {"workload": "serving mix: Poisson arrivals, square grids side in "
                                    "{32..512}, bubble or dressed, D in {3,4}, nodes (256x64)"
                                    "..(2048x256), FP64 or mixed, 40 GB budget"}}
     print(json.dumps(line), flush=True)
     return 0
 
+
+# --------------------------------------------------------------------------
+# executed work and rooflines
+# --------------------------------------------------------------------------
+
+def executed(arith, pairs, pairs_full, nodes):
+    """Thread instructions per pipe (and issued warp instructions) of a launch
+    of the `arith` kernel ('fp64', 'f32x2' or 'bulk32') from its counters."""
+    if EXEC_MODEL is None:
+        return None
+    m = EXEC_MODEL[arith]
+    pc = pairs - pairs_full
+    return {k: m[k][0] * pc + m[k][1] * pairs_full + m[k][2] * nodes for k in m}
+
+
+def fp64_pipe_seconds(ex, peaks):
+    """Time the FP64 pipe needs for the executed DFMA, DMUL and DADD at their
+    measured rates (conversions counted at the DFMA rate)."""
+    return (ex["dfma"] / peaks["dfma_per_s"] + ex["dmul"] / peaks["dmul_per_s"]
+            + ex["dadd"] / peaks["dadd_per_s"] + ex["fp64_other"] / peaks["dfma_per_s"])
+
+
+def fma_pipe_seconds(ex, peaks):
+    """Time the FP32 FMA pipes need for the executed FFMA, FMUL and FADD
+    (paired forms count twice) at the measured FFMA rate."""
+    return ex["fma_ops"] / peaks["ffma_per_s"]
+
+
+# --------------------------------------------------------------------------
+# the library's arm
+# --------------------------------------------------------------------------
 
 def run_gfc(args):
     import torch
@@ -239,14 +346,16 @@ def run_gfc(args):
     dev = torch.device("cuda", local if ws > 1 else 0)
     torch.cuda.set_device(dev)
     import paper_1205_0752_gb300 as gfc
+    import synthetic_inputs as si
+    from paper_1205_0752_gb300 import binding
 
     side = args.side
-    rect, _ = shard_rows(rank, ws, side)
+    rect = shard_rect(rank, ws, side)
     grid = gfc.make_grid(*rect, side, side)
     # --quick --precision P times the headline workload in precision P (for
     # profiling the other kernels on a small case); the full line is FP64
-    par64 = gfc.make_params(dim=4, mu2=1.0, n_radial=NR, n_angular=NA,
-                            precision=args.precision if args.quick else "fp64")
+    prec0 = args.precision if args.quick else "fp64"
+    par64 = gfc.make_params(dim=4, mu2=1.0, n_radial=NR, n_angular=NA, precision=prec0)
     parmx = gfc.make_params(dim=4, mu2=1.0, n_radial=NR, n_angular=NA, precision="mixed")
     props = [gfc.make_prop({"kind": "scalar", "m2": m2}) for m2 in MASSES2]
     outs = [torch.empty((side, side), dtype=torch.complex128, device=dev) for _ in MASSES2]
@@ -267,24 +376,28 @@ def run_gfc(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         return float(t.item())
 
-    def step(params, per_launch=None):
-        for p, G in zip(props, outs):
+    def step(params, per_launch=None, stats=None, props_=None, outs_=None, grid_=None):
+        for k, (p, G) in enumerate(zip(props_ or props, outs_ or outs)):
             if per_launch is not None:
                 a = torch.cuda.Event(enable_timing=True)
                 b = torch.cuda.Event(enable_timing=True)
                 a.record(stream)
-                gfc.eval_grid(p, params, grid, out=G, stream=stream)
+                gfc.eval_grid(p, params, grid_ or grid, out=G, stream=stream)
                 b.record(stream)
-                per_launch.append((a, b))
+                per_launch.setdefault(k, []).append((a, b))
             else:
-                gfc.eval_grid(p, params, grid, out=G, stream=stream)
+                gfc.eval_grid(p, params, grid_ or grid, out=G, stream=stream)
+            if stats is not None:
+                stats.append(gfc.last_stats())    # (synchronises: warm-up only)
 
-    def timed(params, steps, warmup, per_launch=None, clocks=None):
+    def timed(params, steps, warmup, per_launch=None, clocks=None, stats=None, **kw):
+        """K timed steps after W warm-up steps (the first warm-up step records
+        each launch's counters), L2 flushed before every step."""
         if clocks:
             clocks.start()
-        for _ in range(warmup):
+        for w in range(warmup):
             flush.zero_()                     # also loads the fill kernel before timing
-            step(params)
+            step(params, stats=stats if w == 0 else None, **kw)
         torch.cuda.synchronize()
         barrier()
         torch.cuda.synchronize()
@@ -294,7 +407,7 @@ def run_gfc(args):
         e0.record(stream)
         for _ in range(steps):
             flush.zero_()                     # write 256 MB (> L2) between steps
-            step(params, per_launch)
+            step(params, per_launch, **kw)
         e1.record(stream)
         torch.cuda.synchronize()
         tw1 = datetime.datetime.now()
@@ -303,121 +416,112 @@ def run_gfc(args):
         ck = clocks.stop(tw0, tw1) if clocks else None
         return max_over_ranks(e0.elapsed_time(e1) / 1e3), ck
 
+    def launch_seconds(per_launch):
+        """mean CUDA-event seconds of each launch index over the timed steps"""
+        return [float(np.mean([a.elapsed_time(b) for a, b in per_launch[k]])) / 1e3
+                for k in sorted(per_launch)]
+
+    def rel_errors(got, ref):
+        errs = []
+        for a, b in zip(got, ref):
+            a = a.cpu().numpy().ravel() if hasattr(a, "cpu") else np.ravel(a)
+            b = b.cpu().numpy().ravel() if hasattr(b, "cpu") else np.ravel(b)
+            tau = 1e-3 * np.max(np.abs(b))
+            errs.append(np.abs(a - b) / np.maximum(np.abs(b), tau))
+        return np.concatenate(errs)
+
+    # ---- measured pipe rates (the roofline denominators) --------------------
+    peaks = gfc.measure_pipe_peaks(0.2, stream=stream)
+
     # ---- FP64: the headline ------------------------------------------------
-    per_launch = []
+    per_launch, st64 = {}, []
     sampler = ClockSampler(dev.index or 0)
-    t64, clocks = timed(par64, args.steps, args.warmup, per_launch, sampler)
-    launch_ms = [a.elapsed_time(b) for a, b in per_launch]
-    st64 = gfc.last_stats()
-    node_evals_launch = st64.node_evals
+    t64, clocks = timed(par64, args.steps, max(args.warmup, 1), per_launch, sampler, st64)
+    launch_s = launch_seconds(per_launch)
     value = ws * npts_step * args.steps / t64
-    G64 = [G.clone() for G in outs]
     if args.quick:
         if rank == 0:
-            print(json.dumps({"metric": METRIC, "value": ws * npts_step * args.steps / t64,
-                              "unit": "points/s", "quick": True, "side": side,
-                              "precision": args.precision,
-                              "launch_ms": [round(v, 3) for v in launch_ms]}), flush=True)
+            print(json.dumps({"metric": METRIC, "value": value, "unit": "points/s", "quick": True,
+                              "side": side, "precision": args.precision,
+                              "launch_ms": [round(1e3 * v, 3) for v in launch_s]}), flush=True)
         return 0
+    G64 = [G.clone() for G in outs]
+    node_evals_step = sum(s.node_evals for s in st64)
 
-    # ---- mixed precision study --------------------------------------------
-    per_launch_mx = []
-    tmx, _ = timed(parmx, args.steps, 1, per_launch_mx)
-    stmx = gfc.last_stats()
+    def roofline_fp64(stats, secs):
+        """FP64-pipe fraction of the FP64 kernel over the given launches."""
+        out = {"algorithmic_node_evals": int(sum(s.node_evals for s in stats)),
+               "pairs_evaluated": int(sum(s.pairs_evaluated for s in stats)),
+               "pairs_full_table": int(sum(s.pairs_full_table for s in stats)),
+               "seconds": float(sum(secs))}
+        out["effective_tflops"] = FLOP_PER_NODE_EVAL * out["algorithmic_node_evals"] / out["seconds"] / 1e12
+        ex = [executed("fp64", s.pairs_evaluated, s.pairs_full_table, s.node_evals // (2 * NA // 2))
+              for s in stats]
+        if ex[0] is not None:
+            busy = sum(fp64_pipe_seconds(e, peaks) for e in ex)
+            fl = sum(2 * e["dfma"] + e["dmul"] + e["dadd"] for e in ex)
+            out.update(pipe_frac=busy / out["seconds"], executed_tflops=fl / out["seconds"] / 1e12,
+                       fp64_pipe_inst=float(sum(e["dfma"] + e["dmul"] + e["dadd"] + e["fp64_other"]
+                                                for e in ex)))
+        return out
+
+    rf = roofline_fp64(st64, launch_s)
+    peak_fma_tflops = 2 * peaks["dfma_per_s"] / 1e12
+    frac = rf.get("pipe_frac")
+    roofline = {
+        "bound": "alu", "kernel": "eval_kernel<double,128,1,0>",
+        "unit": "TFLOP/s",
+        # FMA-equivalent rate: every FP64-pipe instruction counted as one FMA
+        # slot (2 flop) at the measured DFMA/DMUL/DADD rates, so that
+        # achieved/peak is the FP64 pipe's busy fraction
+        "achieved": frac * peak_fma_tflops if frac is not None else None,
+        "peak": peak_fma_tflops,
+        "frac": frac,
+        "traffic": TRAFFIC_PER_POINT * side * side if TRAFFIC_PER_POINT else None,
+        "peak_source": "measured on this device by gfc_measure_pipe_peaks (DFMA chains, best "
+                       "of 4 launch shapes); of measured",
+        "executed_tflops": rf.get("executed_tflops"),
+        "effective_tflops": rf["effective_tflops"],
+        "effective_note": "11 flop per algorithmic node-eval of the 2048x256 quadrature over "
+                          "the kernel time; the compressed angular rules evaluate "
+                          "pairs_evaluated of the node_evals/2 pairs for the same sums, so this "
+                          "rate is not bounded by the pipe",
+        "pairs_evaluated_per_step": rf["pairs_evaluated"],
+        "pairs_full_table_per_step": rf["pairs_full_table"],
+        "algorithmic_pairs_per_step": rf["algorithmic_node_evals"] // 2,
+        "per_mass": [dict(m2=m2, launch_ms=1e3 * s,
+                          pipe_frac=roofline_fp64([st], [s]).get("pipe_frac"))
+                     for m2, st, s in zip(MASSES2, st64, launch_s)],
+        "measured_peaks": peaks,
+    }
+
+    # ---- mixed precision ---------------------------------------------------
+    def mixed_roofline(stats, secs, fallback):
+        """Issue and pipe fractions of a mixed step: the binary32 bulk and the
+        fallback kernel (double-float or FP64) together."""
+        if EXEC_MODEL is None:
+            return {}
+        fma_s = fp64_s = 0.0
+        for s in stats:
+            nodes_fb = s.node_evals_fallback // NA
+            nodes_b = s.node_evals // NA - nodes_fb
+            eb = executed("bulk32", s.pairs_evaluated - s.pairs_fallback,
+                          s.pairs_full_table - s.pairs_full_table_fallback, nodes_b)
+            ef = executed("f32x2" if fallback == "f32x2" else "fp64", s.pairs_fallback,
+                          s.pairs_full_table_fallback, nodes_fb)
+            fma_s += fma_pipe_seconds(eb, peaks) + (fma_pipe_seconds(ef, peaks)
+                                                    if fallback == "f32x2" else 0.0)
+            fp64_s += fp64_pipe_seconds(eb, peaks) + fp64_pipe_seconds(ef, peaks)
+        T = float(sum(secs))
+        return {"fma_pipe_frac": fma_s / T, "fp64_pipe_frac": fp64_s / T,
+                "peak_ffma_tflops": 2 * peaks["ffma_per_s"] / 1e12}
+
+    per_launch_mx, stmx = {}, []
+    tmx, _ = timed(parmx, args.steps, 1, per_launch_mx, stats=stmx)
     mixed_value = ws * npts_step * args.steps / tmx
-    errs = []
-    for Gm, Gd in zip(outs, G64):
-        a = Gm.cpu().numpy().ravel()
-        b = Gd.cpu().numpy().ravel()
-        tau = 1e-3 * np.max(np.abs(b))
-        errs.append(np.abs(a - b) / np.maximum(np.abs(b), tau))
-    err = np.concatenate(errs)
+    err = rel_errors(outs, G64)
     abs_err = np.concatenate([np.abs(Gm.cpu().numpy().ravel() - Gd.cpu().numpy().ravel())
                               for Gm, Gd in zip(outs, G64)])
-    fp64_frac = stmx.points_fp64 / max(1, stmx.points)
-
-    # ---- double-float: FP64-class accuracy on the binary32 pipes ----------
-    pardf = gfc.make_params(dim=4, mu2=1.0, n_radial=NR, n_angular=NA, precision="f32x2")
-    tdf, _ = timed(pardf, args.steps, 1)
-    df_value = ws * npts_step * args.steps / tdf
-    errs_df = []
-    for Gm, Gd in zip(outs, G64):
-        a = Gm.cpu().numpy().ravel()
-        b = Gd.cpu().numpy().ravel()
-        tau = 1e-3 * np.max(np.abs(b))
-        errs_df.append(np.abs(a - b) / np.maximum(np.abs(b), tau))
-    err_df = np.concatenate(errs_df)
-    # mixed precision whose routed points use the FP64 kernel
-    parmd = gfc.make_params(dim=4, mu2=1.0, n_radial=NR, n_angular=NA, precision="mixed",
-                            mixed_fallback="fp64")
-    tmd, _ = timed(parmd, args.steps, 1)
-    md_value = ws * npts_step * args.steps / tmd
-    errs_md = []
-    for Gm, Gd in zip(outs, G64):
-        a = Gm.cpu().numpy().ravel()
-        b = Gd.cpu().numpy().ravel()
-        tau = 1e-3 * np.max(np.abs(b))
-        errs_md.append(np.abs(a - b) / np.maximum(np.abs(b), tau))
-    err_md = np.concatenate(errs_md)
-
-    # ---- the paper's angular rule: 49-node tanh-sinh in z (Sect. 4) --------
-    paper_rule = {}
-    for prec in ("fp64", "f32x2", "mixed"):
-        parts = gfc.make_params(dim=4, mu2=1.0, n_radial=NR, n_angular=49,
-                                angular_rule="tanh-sinh", precision=prec)
-        tts, _ = timed(parts, 1, 1)
-        paper_rule[prec] = ws * npts_step / tts
-
-    # ---- the psi integral in closed form (no angular quadrature error) -----
-    exact_rule = {}
-    for nr in (NR, 4 * NR):
-        for prec in ("fp64", "f32x2", "mixed"):
-            parex = gfc.make_params(dim=4, mu2=1.0, n_radial=nr, n_angular=2,
-                                    angular_rule="exact", precision=prec)
-            tex, _ = timed(parex, 1, 1)
-            exact_rule[f"{prec}_nr{nr}"] = ws * npts_step / tex
-
-    # ---- near-axis accuracy: closed-form angle + clustered radial rule -----
-    clustered = {}
-    for prec in ("fp64", "f32x2", "mixed"):
-        parcl = gfc.make_params(dim=4, mu2=1.0, n_radial=NR, n_angular=2, angular_rule="exact",
-                                radial_rule="clustered", precision=prec)
-        tcl, _ = timed(parcl, 1, 1)
-        clustered[prec] = ws * npts_step / tcl
-
-    # ---- Step 3 diagnostics: region-1 map and the y-plane map of B --------
-    diag = {}
-    xg = gfc.grid_points((*rect, side, side), stream=stream).reshape(-1)
-    for name, fn in (("region_map_points_per_s", lambda: gfc.region_map(props[1], xg, stream=stream)),
-                     ("angular_map_gl256_y_per_s",
-                      lambda: gfc.angular_map(props[1], par64, -2.0 + 1.0j, xg, stream=stream)),
-                     ("angular_map_exact_y_per_s",
-                      lambda: gfc.angular_map(props[1], gfc.make_params(angular_rule="exact"),
-                                              -2.0 + 1.0j, xg, stream=stream))):
-        fn()
-        a_ev, b_ev = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a_ev.record(stream)
-        fn()
-        b_ev.record(stream)
-        torch.cuda.synchronize()
-        diag[name] = xg.numel() / (a_ev.elapsed_time(b_ev) / 1e3)
-
-    # ---- end to end through the host-buffer C-ABI call --------------------
-    # the block's grid points, made by the library's own Kernel 1 and held in
-    # pinned host memory before the timed region
-    xh = gfc.grid_points((*rect, side, side), stream=stream).reshape(-1).cpu().pin_memory()
-    Gh = torch.empty_like(xh).pin_memory()
-    for _ in range(1):
-        for p in props:
-            gfc.eval_points_host(p, par64, xh, Gh, stream=stream)
-    barrier()
-    t0 = time.perf_counter()
-    e2e_steps = max(1, min(args.steps, 2))
-    for _ in range(e2e_steps):
-        for p in props:
-            gfc.eval_points_host(p, par64, xh, Gh, stream=stream)
-    e2e_t = max_over_ranks(time.perf_counter() - t0)
-    e2e_value = ws * npts_step * e2e_steps / e2e_t
 
     def decade_hist(e):
         """counts of relative errors per decade from 1e-15 to 1e-6, plus the
@@ -427,73 +531,84 @@ def run_gfc(args):
         names = ["<1e-15"] + [f"1e{k}..1e{k + 1}" for k in range(-15, -6)] + [">=1e-6"]
         return dict(zip(names, (int(v) for v in counts)))
 
-    # ---- roofline of the dominant kernel ----------------------------------
-    avg_launch_s = float(np.mean(launch_ms)) / 1e3
-    achieved = FLOP_PER_NODE_EVAL * node_evals_launch / avg_launch_s / 1e12
-    peak64 = SM_COUNT * FP64_FMA_PER_SM_CLK * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    mixed = {"value": mixed_value, "unit": "points/s", "ms_per_step": 1e3 * tmx / args.steps,
+             "max_rel_err": float(err.max()), "p99_rel_err": float(np.percentile(err, 99)),
+             "median_rel_err": float(np.median(err)), "max_abs_err": float(abs_err.max()),
+             "frac_rel_err_gt_1e-6": float(np.mean(err > 1e-6)),
+             "rel_err_hist": decade_hist(err),
+             "error_vs": "FP64 GPU results (parity <= 1e-10 with the oracle)",
+             "fallback": "double-float (f32x2)",
+             "routed_fraction_per_mass": [dict(m2=m2, points_routed=s.points_fp64 / s.points,
+                                               fallback_node_evals=s.node_evals_fallback / max(1, s.node_evals))
+                                          for m2, s in zip(MASSES2, stmx)],
+             "per_mass_ms": [1e3 * s for s in launch_seconds(per_launch_mx)],
+             **mixed_roofline(stmx, launch_seconds(per_launch_mx), "f32x2")}
+
+    # ---- double-float: FP64-class accuracy on the binary32 pipes ----------
+    pardf = gfc.make_params(dim=4, mu2=1.0, n_radial=NR, n_angular=NA, precision="f32x2")
+    per_launch_df, stdf = {}, []
+    tdf, _ = timed(pardf, args.steps, 1, per_launch_df, stats=stdf)
+    err_df = rel_errors(outs, G64)
+    f32x2 = {"value": ws * npts_step * args.steps / tdf, "unit": "points/s",
+             "ms_per_step": 1e3 * tdf / args.steps,
+             "max_rel_err": float(err_df.max()), "median_rel_err": float(np.median(err_df)),
+             "rel_err_hist": decade_hist(err_df), "error_vs": "FP64 GPU results",
+             "arith": "double-float (pairs of binary32) on the binary32 pipes"}
+    if EXEC_MODEL is not None:
+        T = sum(launch_seconds(per_launch_df))
+        ex = [executed("f32x2", s.pairs_evaluated, s.pairs_full_table, s.node_evals // NA) for s in stdf]
+        f32x2["fma_pipe_frac"] = sum(fma_pipe_seconds(e, peaks) for e in ex) / T
+
+    # mixed precision whose routed work uses the FP64 kernel
+    parmd = gfc.make_params(dim=4, mu2=1.0, n_radial=NR, n_angular=NA, precision="mixed",
+                            mixed_fallback="fp64")
+    nmd = max(3, min(args.steps, 5))
+    tmd, _ = timed(parmd, nmd, 1)
+    err_md = rel_errors(outs, G64)
+    mixed_fp64 = {"value": ws * npts_step * nmd / tmd, "unit": "points/s", "steps": nmd,
+                  "ms_per_step": 1e3 * tmd / nmd, "max_rel_err": float(err_md.max()),
+                  "frac_rel_err_gt_1e-6": float(np.mean(err_md > 1e-6))}
+
+    # ---- end to end through the host-buffer C-ABI call --------------------
+    # the block's grid points, made by the library's own Kernel 1 and held in
+    # pinned host memory before the timed region; the same K steps as `value`
+    xh = gfc.grid_points((*rect, side, side), stream=stream).reshape(-1).cpu().pin_memory()
+    Gh = torch.empty_like(xh).pin_memory()
+    for p in props:
+        gfc.eval_points_host(p, par64, xh, Gh, stream=stream)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        for p in props:
+            gfc.eval_points_host(p, par64, xh, Gh, stream=stream)
+    e2e_t = max_over_ranks(time.perf_counter() - t0)
+    e2e_value = ws * npts_step * args.steps / e2e_t
+
     line = {
         "metric": METRIC, "value": value, "unit": "points/s", "n_gpus": ws,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t64 / args.steps,
+        "steps": args.steps, "warmup": max(args.warmup, 1), "ms_per_step": 1e3 * t64 / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
         "config": {"workload": WORKLOAD,
-                   "points_per_step": ws * npts_step, "node_evals_per_step": 3 * node_evals_launch * ws,
+                   "points_per_step": ws * npts_step, "node_evals_per_step": node_evals_step * ws,
                    "l2": "256 MB buffer written before every step (> 129 MB L2)",
-                   "parallelism": f"rows sharded over {ws} GPU(s), no collective"},
-        "node_evals_per_s": 3 * node_evals_launch * ws * args.steps / t64,
+                   "parallelism": f"rows interleaved over {ws} GPU(s) (rank r: rows r mod {ws}), "
+                                  "no collective"},
+        "node_evals_per_s": node_evals_step * ws * args.steps / t64,
         "clocks": clocks,
         "gpu_launches": 2 * 3 * args.steps,
-        "roofline": {"bound": "alu", "kernel": "eval_kernel<double,128,1>",
-                     "achieved": achieved, "peak": peak64, "unit": "TFLOP/s",
-                     "frac": achieved / peak64, "traffic": TRAFFIC_PER_POINT * side * side,
-                     "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one "
-                                       "256x256 launch (243,456 B), scaled by points per launch",
-                     "peak_source": "derived: 152 SM x 2 FP64 FMA/clk x 2 flop x 2070 MHz "
-                                    "(ncu: dfma peak_sustained 304/clk = 152 x 2)",
-                     "algorithmic": "11 flop per node-eval (22 per +-psi pair)",
-                     "executed_pairs_per_launch": st64.pairs_evaluated,
-                     "algorithmic_pairs_per_launch": node_evals_launch // 2,
-                     "executed_fraction": st64.pairs_evaluated / max(1, node_evals_launch // 2),
-                     "executed_tflops": 2 * FLOP_PER_NODE_EVAL * st64.pairs_evaluated / avg_launch_s / 1e12,
-                     "executed_frac": 2 * FLOP_PER_NODE_EVAL * st64.pairs_evaluated / avg_launch_s / 1e12 / peak64,
-                     "note": "compressed angular rules evaluate executed_fraction of the "
-                             "algorithmic pairs for the same sums (to rounding), so the "
-                             "algorithmic rate exceeds the FP64 pipe peak; executed_frac counts "
-                             "the same 22 flop per pair actually evaluated; ncu shows the FP64 "
-                             "pipe 89.6% busy (profiles/eval_kernel_fp64_production_bubble.md)"},
-        "mixed": {"value": mixed_value, "unit": "points/s", "ms_per_step": 1e3 * tmx / args.steps,
-                  "max_rel_err": float(err.max()), "p99_rel_err": float(np.percentile(err, 99)),
-                  "median_rel_err": float(np.median(err)), "max_abs_err": float(abs_err.max()),
-                  "frac_rel_err_gt_1e-6": float(np.mean(err > 1e-6)),
-                  "rel_err_hist": decade_hist(err),
-                  "fp64_point_fraction": fp64_frac,
-                  "error_vs": "FP64 GPU results (parity <= 1e-10 with the oracle)",
-                  "fp32_peak_tflops": SM_COUNT * FP32_FMA_PER_SM_CLK * 2 * SM_MAX_MHZ * 1e6 / 1e12,
-                  "achieved_tflops": FLOP_PER_NODE_EVAL * 3 * node_evals_launch * args.steps / tmx / 1e12},
-        "f32x2": {"value": df_value, "unit": "points/s", "ms_per_step": 1e3 * tdf / args.steps,
-                  "max_rel_err": float(err_df.max()), "median_rel_err": float(np.median(err_df)),
-                  "rel_err_hist": decade_hist(err_df),
-                  "error_vs": "FP64 GPU results",
-                  "arith": "double-float (pairs of binary32) on the binary32 pipes"},
-        "mixed_fp64_fallback": {"value": md_value, "unit": "points/s",
-                                 "ms_per_step": 1e3 * tmd / args.steps,
-                                 "max_rel_err": float(err_md.max()),
-                                 "frac_rel_err_gt_1e-6": float(np.mean(err_md > 1e-6))},
-        "paper_angular_rule": {"rule": "tanh-sinh, 49 nodes in z = cos psi (Sect. 4)",
-                               "n_radial": NR, "unit": "points/s",
-                               "fp64": paper_rule["fp64"], "f32x2": paper_rule["f32x2"],
-                               "mixed": paper_rule["mixed"]},
-        "exact_angular": dict({"rule": "psi integral in closed form (limit of every angular "
-                                         "rule); radial Gauss-Legendre n_radial as named",
-                               "unit": "points/s"}, **exact_rule),
-        "clustered_radial": dict({"rule": "closed-form angle, radial rule sinh-clustered at the "
-                                          "pole nearest the ray (n_radial 2048)",
-                                  "unit": "points/s"}, **clustered),
-        "diagnostics": dict({"grid": f"{side}x{side} x (region map) or y (map of B at x = -2 + i)",
-                             "propagator": "bubble m = 1"}, **diag),
-        "e2e": {"value": e2e_value, "unit": "points/s", "h2d_bytes_per_step": 3 * 16 * side * side,
+        "roofline": roofline,
+        "mixed": mixed,
+        "f32x2": f32x2,
+        "mixed_fp64_fallback": mixed_fp64,
+        "e2e": {"value": e2e_value, "unit": "points/s", "steps": args.steps,
+                "h2d_bytes_per_step": 3 * 16 * side * side,
                 "d2h_bytes_per_step": 3 * 16 * side * side},
     }
+
+    if ws == 1 and not args.no_studies:
+        line.update(single_gpu_studies(gfc, si, torch, stream, flush, timed, rel_errors, peaks,
+                                       par64, props, rect, side, args))
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         v, dt = oracle_points_per_s(args.ref_points)
         line["cpu_baseline"] = {"value": v, "unit": "points/s", "cores": cpu_cores(),
@@ -508,6 +623,114 @@ def run_gfc(args):
     return 0
 
 
+def single_gpu_studies(gfc, si, torch, stream, flush, timed, rel_errors, peaks, par64, props,
+                       rect, side, args):
+    """The other workload configurations, the paper's angular rules, the
+    closed-form angle, the clustered radial rule, the Step 3 diagnostics and
+    the serving mix (one GPU)."""
+    import oracle
+    dev = torch.device("cuda", torch.cuda.current_device())
+    out = {}
+    nst = max(5, min(args.steps, 10))
+
+    # ---- every workload configuration: points/s and error vs the oracle ----
+    a, b, c = si.dressed_draws(3, 1)[0]
+    dressed = {"kind": "dressed", "a": a, "b": b, "c": c}
+    cases = [
+        ("paper_example_128x128", {"kind": "cpair", "mk2": 0.5j, "mq2": -0.5j},
+         dict(dim=4, mu2=0.0, n_radial=256, n_angular=64), si.grid_rect("paper"), 128, 1024),
+        ("bubble_64x64", {"kind": "scalar", "m2": 1.0},
+         dict(dim=4, mu2=1.0, n_radial=256, n_angular=64), si.grid_rect("small"), 64, 4096),
+        ("dressed_512x512_D3", dressed, dict(dim=3, mu2=1.0, n_radial=1024, n_angular=128),
+         si.grid_rect("small"), 512, 256),
+        ("dressed_512x512_D4", dressed, dict(dim=4, mu2=1.0, n_radial=1024, n_angular=128),
+         si.grid_rect("small"), 512, 256),
+    ]
+    configs = {}
+    for name, prop, par, crect, n, nsample in cases:
+        g = gfc.make_grid(*crect, n, n)
+        x = oracle.grid_points(*crect, n, n)
+        idx = si.sample_indices(11, n * n, min(nsample, n * n))
+        ref = oracle.eval_points(prop, par, x[idx])
+        rec = {"points": n * n, "nodes": f"{par['n_radial']}x{par['n_angular']}", "D": par["dim"],
+               "steps": nst, "oracle_sample": int(idx.size)}
+        for prec in ("fp64", "mixed"):
+            pp = gfc.make_params(dict(par, precision=prec))
+            G = torch.empty((n, n), dtype=torch.complex128, device=dev)
+            per, st = {}, []
+            t, _ = timed(pp, nst, 2, per, stats=st, props_=[gfc.make_prop(prop)], outs_=[G],
+                         grid_=g)
+            e = rel_errors([G.cpu().numpy().ravel()[idx]], [ref])
+            r = {"points_per_s": n * n * nst / t, "max_rel_err_vs_oracle": float(e.max())}
+            if prec == "fp64" and EXEC_MODEL is not None and prop["kind"] == "scalar":
+                # (the model is calibrated on ray nodes of the scalar bubble)
+                s = st[0]
+                ex = executed("fp64", s.pairs_evaluated, s.pairs_full_table,
+                              s.node_evals // (2 * ((par["n_angular"] + 1) // 2)))
+                r["fp64_pipe_frac"] = fp64_pipe_seconds(ex, peaks) / (t / nst)
+            rec[prec] = r
+        configs[name] = rec
+    out["configs"] = configs
+
+    # ---- the paper's angular rule: 49-node tanh-sinh in z (Sect. 4) --------
+    paper_rule = {}
+    for prec in ("fp64", "f32x2", "mixed"):
+        parts = gfc.make_params(dim=4, mu2=1.0, n_radial=NR, n_angular=49,
+                                angular_rule="tanh-sinh", precision=prec)
+        tts, _ = timed(parts, 3, 1)
+        paper_rule[prec] = 3 * len(MASSES2) * side * side / tts
+    out["paper_angular_rule"] = dict({"rule": "tanh-sinh, 49 nodes in z = cos psi (Sect. 4)",
+                                      "n_radial": NR, "unit": "points/s", "steps": 3}, **paper_rule)
+
+    # ---- the psi integral in closed form (no angular quadrature error) -----
+    exact_rule = {}
+    for nr in (NR, 4 * NR):
+        for prec in ("fp64", "f32x2", "mixed"):
+            parex = gfc.make_params(dim=4, mu2=1.0, n_radial=nr, n_angular=2,
+                                    angular_rule="exact", precision=prec)
+            tex, _ = timed(parex, 3, 1)
+            exact_rule[f"{prec}_nr{nr}"] = 3 * len(MASSES2) * side * side / tex
+    out["exact_angular"] = dict({"rule": "psi integral in closed form (limit of every angular "
+                                         "rule); radial Gauss-Legendre n_radial as named",
+                                 "unit": "points/s", "steps": 3}, **exact_rule)
+
+    # ---- near-axis accuracy: closed-form angle + clustered radial rule -----
+    clustered = {}
+    for prec in ("fp64", "f32x2", "mixed"):
+        parcl = gfc.make_params(dim=4, mu2=1.0, n_radial=NR, n_angular=2, angular_rule="exact",
+                                radial_rule="clustered", precision=prec)
+        tcl, _ = timed(parcl, 3, 1)
+        clustered[prec] = 3 * len(MASSES2) * side * side / tcl
+    out["clustered_radial"] = dict({"rule": "closed-form angle, radial rule sinh-clustered at the "
+                                            "pole nearest the ray (n_radial 2048)",
+                                    "unit": "points/s", "steps": 3}, **clustered)
+
+    # ---- Step 3 diagnostics: region-1 map and the y-plane map of B --------
+    diag = {}
+    xg = gfc.grid_points((*rect, side, side), stream=stream).reshape(-1)
+    for name, fn in (("region_map_points_per_s", lambda: gfc.region_map(props[1], xg, stream=stream)),
+                     ("angular_map_gl256_y_per_s",
+                      lambda: gfc.angular_map(props[1], par64, -2.0 + 1.0j, xg, stream=stream)),
+                     ("angular_map_exact_y_per_s",
+                      lambda: gfc.angular_map(props[1], gfc.make_params(angular_rule="exact"),
+                                              -2.0 + 1.0j, xg, stream=stream))):
+        fn()
+        a_ev, b_ev = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a_ev.record(stream)
+        for _ in range(3):
+            fn()
+        b_ev.record(stream)
+        torch.cuda.synchronize()
+        diag[name] = 3 * xg.numel() / (a_ev.elapsed_time(b_ev) / 1e3)
+    out["diagnostics"] = dict({"grid": f"{side}x{side} x (region map) or y (map of B at x = -2 + i)",
+                               "propagator": "bubble m = 1", "steps": 3}, **diag)
+
+    # ---- serving: continuous batching --------------------------------------
+    if not args.no_serve:
+        out["serve"] = serve_study(gfc, n_spec=args.serve_requests, rate=args.serve_rate)
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -517,6 +740,9 @@ def main():
     # ~13 s of the oracle on 16 host cores (3 x 6144 points at ~1.4e3 points/s)
     ap.add_argument("--ref-points", type=int, default=6144)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-studies", action="store_true",
+                    help="leave out the other configurations, rule studies and serving")
+    ap.add_argument("--no-serve", action="store_true", help="leave out the serving runs")
     ap.add_argument("--side", type=int, default=SIDE,
                     help="grid side per GPU (the benchmark workload is 1024)")
     ap.add_argument("--quick", action="store_true",
@@ -529,6 +755,8 @@ def main():
     ap.add_argument("--serve-log", default=None,
                     help="with --serve: write one JSON line per request to this file")
     args = ap.parse_args()
+    if args.gpus > 1 and "WORLD_SIZE" not in os.environ:
+        return relaunch(args.gpus, sys.argv[1:]).returncode
     if args.impl == "reference":
         return run_reference(args)
     if args.serve:

@@ -323,7 +323,8 @@ int gfc_last_stats(gfc_eval_stats *out);
  * runs 8 or 16 independent dependency chains per thread on SMs x 4 or 8
  * blocks of 256 threads (the best of these configurations, each the best of
  * two timed launches of about seconds/4 after a calibration run, CUDA events
- * on `stream`): binary64 FMA, multiply and add (the FP64 pipe), binary32 FMA
+ * on `stream`): binary64 FMA (plain chains, and chains interleaved with an
+ * independent binary32 FMA chain), multiply and add (the FP64 pipe), binary32 FMA
  * (the FMA pipe) and rcp.approx.ftz.f32 (the special-function unit). These
  * are the denominators of the kernels' executed-work fractions. Blocks until
  * the probes have finished (about 10 x seconds). GFC_EINVAL for out = NULL or
@@ -335,6 +336,9 @@ typedef struct {
     double ffma_per_s;     /* binary32 fused multiply-adds per second          */
     double rcp32_per_s;    /* binary32 approximate reciprocals per second      */
     int sm_count;          /* multiprocessors of the device                    */
+    double dfma_mhz;       /* SM clock during the best binary64 FMA launch
+                              (clock64 over the global timer on one SM)        */
+    double ffma_mhz;       /* the same for the binary32 FMA launch             */
 } gfc_pipe_peaks;
 int gfc_measure_pipe_peaks(gfc_pipe_peaks *out, double seconds, void *stream);
 

@@ -70,7 +70,8 @@ class _ServerStats(ctypes.Structure):
 class _PipePeaks(ctypes.Structure):
     _fields_ = [("dfma_per_s", ctypes.c_double), ("dmul_per_s", ctypes.c_double),
                 ("dadd_per_s", ctypes.c_double), ("ffma_per_s", ctypes.c_double),
-                ("rcp32_per_s", ctypes.c_double), ("sm_count", ctypes.c_int)]
+                ("rcp32_per_s", ctypes.c_double), ("sm_count", ctypes.c_int),
+                ("dfma_mhz", ctypes.c_double), ("ffma_mhz", ctypes.c_double)]
 
 
 class _RequestInfo(ctypes.Structure):
@@ -334,7 +335,8 @@ def measure_pipe_peaks(seconds: float = 0.2, stream=None) -> dict:
     _check(load_library().gfc_measure_pipe_peaks(ctypes.byref(p), float(seconds), _stream_ptr(stream)),
            "gfc_measure_pipe_peaks")
     return {"dfma_per_s": p.dfma_per_s, "dmul_per_s": p.dmul_per_s, "dadd_per_s": p.dadd_per_s,
-            "ffma_per_s": p.ffma_per_s, "rcp32_per_s": p.rcp32_per_s, "sm_count": p.sm_count}
+            "ffma_per_s": p.ffma_per_s, "rcp32_per_s": p.rcp32_per_s, "sm_count": p.sm_count,
+            "dfma_mhz": p.dfma_mhz, "ffma_mhz": p.ffma_mhz}
 
 
 # --------------------------------------------------------------------------
