@@ -76,8 +76,13 @@ typedef struct {
 typedef enum {
     GFC_FP64 = 0,    /* every step in IEEE binary64                            */
     GFC_MIXED = 1,   /* angular sums and per-node set-up in binary32 with
-                        compensated binary32 radial sums; binary64 for the
-                        epilogue and for every point in the binary64 band     */
+                        compensated binary32 radial sums, binary64 for the
+                        epilogue; the points of the cut band whole in
+                        binary64; a point whose estimated binary32 error is
+                        above mixed_rtol |G| has the node groups with the
+                        largest share of that estimate evaluated again in the
+                        mixed_fallback arithmetic (all of its nodes next to
+                        an angular pinch)                                    */
     GFC_F32X2 = 2    /* every step in double-float arithmetic (a value is the
                         sum of two binary32 numbers, ~48 bits) on the binary32
                         pipes; same tolerance target as GFC_FP64               */
@@ -131,18 +136,24 @@ typedef struct {
                               below half the pole's modulus (paper: 0.1)       */
     int precision;         /* gfc_precision                                    */
     double cut_band;       /* MIXED: points closer than this to a branch cut
-                              half-line are evaluated in binary64 (0.05)       */
+                              half-line are evaluated whole in binary64 (0.05) */
     double pinch_angle;    /* MIXED: points whose radial ray lies within this
                               angle (radians) of a leg's pinch direction are
-                              evaluated in binary64 (default 0: off)           */
+                              evaluated whole in binary64 (default 0: off)     */
     double mixed_rtol;     /* MIXED: a point whose binary32 sum has an
-                              estimated rounding error above mixed_rtol |G| is
-                              evaluated again in binary64 (default 1e-6;
-                              0 turns this off, leaving the cut band only)     */
-    int mixed_fallback;    /* MIXED: arithmetic of the points routed out of
-                              binary32: GFC_F32X2 (default: double-float,
-                              ~48 bits, 2-3x the GB300's FP64 rate) or
-                              GFC_FP64                                          */
+                              estimated rounding error above mixed_rtol |G|
+                              has its node groups (a group: gsz x 32
+                              consecutive radial nodes, at most 32 groups per
+                              point) with the largest share of the estimate
+                              evaluated again in the mixed_fallback
+                              arithmetic, until the estimate of the groups
+                              kept in binary32 is below mixed_rtol |G| / 4
+                              (default 1e-6; 0 turns this off, leaving the cut
+                              band only). The serving runtime evaluates such
+                              points whole in the mixed_fallback arithmetic. */
+    int mixed_fallback;    /* MIXED: arithmetic of what is evaluated again:
+                              GFC_F32X2 (default: double-float, ~48 bits,
+                              about 5x the GB300's FP64 rate) or GFC_FP64     */
     int angular_rule;      /* gfc_angular_rule (default Gauss-Legendre)        */
     int radial_rule;       /* gfc_radial_rule (default mapped half-line)       */
 } gfc_params;
@@ -158,8 +169,9 @@ typedef struct {
 /* Per-call counters of the last evaluation on this thread. */
 typedef struct {
     int64_t points;            /* points of the call                           */
-    int64_t points_fp64;       /* MIXED: points evaluated in binary64 (cut band
-                                  and a-posteriori routing); FP64: all          */
+    int64_t points_fp64;       /* MIXED: points evaluated whole in binary64
+                                  (the cut band, points next to a pinch);
+                                  FP64: all                                    */
     int64_t node_evals;        /* sum over evaluated points of contour nodes x
                                   angular nodes (all passes; binary32 and
                                   binary64 evaluations both counted)            */
@@ -168,13 +180,20 @@ typedef struct {
                                   compressed angular rules make this smaller
                                   than node_evals / 2 at the same result        */
     int64_t node_evals_fallback;  /* MIXED: the part of node_evals evaluated by
-                                  the fallback arithmetic; else 0               */
+                                  the fallback arithmetic (the re-evaluated
+                                  node groups of routed points); else 0         */
     int64_t pairs_fallback;    /* MIXED: the part of pairs_evaluated evaluated
                                   by the fallback arithmetic; else 0            */
     int64_t pairs_full_table;  /* the part of pairs_evaluated summed over the
                                   full angular table (nodes next to a pinch,
                                   where no compressed rule is exact)            */
     int64_t pairs_full_table_fallback;  /* MIXED: the fallback's part of it     */
+    int64_t points_partial;    /* MIXED: routed points whose worst node groups
+                                  were re-evaluated in the fallback arithmetic  */
+    int64_t node_evals_list64; /* MIXED: node evaluations of the points
+                                  evaluated whole in binary64                   */
+    int64_t pairs_list64;      /* MIXED: their angular pairs                    */
+    int64_t pairs_full_table_list64;  /* MIXED: the full-table part of those    */
 } gfc_eval_stats;
 
 const char *gfc_strerror(int status);
@@ -201,10 +220,13 @@ int gfc_eval_points(const gfc_propagator *prop, const gfc_params *params,
  * factor, (|x| + |y|)/|a| for the angular denominator and, in binary32
  * (GFC_MIXED), |w|/min_j |1 - w t_j| for the angular sum. The rounding error
  * of a point is a small multiple of the unit roundoff of its precision times
- * this number. Double-float computes no scale and writes 0: all points under
- * GFC_F32X2, and under GFC_MIXED the points re-evaluated by a GFC_F32X2
- * fallback (a GFC_FP64 fallback writes its binary64 scale). 0 is also written
- * where nothing is summed (the cut side, x = mu2). */
+ * this number. Double-float computes no scale and writes 0 for every point
+ * under GFC_F32X2. Under GFC_MIXED the scale is that of the part of the sum
+ * kept in binary32 (the whole point, or the kept node groups of a point whose
+ * other groups the fallback evaluated again; 0 where nothing is kept, next
+ * to an angular pinch), and the binary64 scale for the cut band, evaluated
+ * whole in binary64. 0 is also written where nothing is summed (the cut side,
+ * x = mu2). */
 int gfc_eval_points_cond(const gfc_propagator *prop, const gfc_params *params,
                          const double *x, int64_t npts, double *G, double *cond, void *stream);
 
@@ -229,7 +251,7 @@ int gfc_eval_points_host(const gfc_propagator *prop, const gfc_params *params,
  * plan), or code that must not pay for the device-wide synchronisation that
  * cudaFree (and often cudaMalloc) implies. The paper has no counterpart.
  * Its node tables and scratch live in one file-scope device array of about
- * 150 KB, so the call allocates nothing (no cudaMalloc, cudaFree or
+ * 170 KB, so the call allocates nothing (no cudaMalloc, cudaFree or
  * allocating library call); x and G are the caller's DEVICE arrays as for
  * gfc_eval_points. Limits: precision GFC_FP64, n_radial <= 4096, even
  * n_angular <= 512, the Gauss-Legendre angular rule and the mapped radial
@@ -339,6 +361,10 @@ typedef struct {
     double dfma_mhz;       /* SM clock during the best binary64 FMA launch
                               (clock64 over the global timer on one SM)        */
     double ffma_mhz;       /* the same for the binary32 FMA launch             */
+    double fp64_mix_per_s; /* binary64 FMA, multiply and add in the proportions
+                              5 : 2 : 1 of the binary64 evaluation kernel, FP64
+                              instructions per second (the FP64 pipe issues a
+                              mixed stream faster than one operation alone)   */
 } gfc_pipe_peaks;
 int gfc_measure_pipe_peaks(gfc_pipe_peaks *out, double seconds, void *stream);
 

@@ -55,7 +55,9 @@ class _EvalStats(ctypes.Structure):
                 ("node_evals", ctypes.c_int64), ("kernel_launches", ctypes.c_int),
                 ("pairs_evaluated", ctypes.c_int64), ("node_evals_fallback", ctypes.c_int64),
                 ("pairs_fallback", ctypes.c_int64), ("pairs_full_table", ctypes.c_int64),
-                ("pairs_full_table_fallback", ctypes.c_int64)]
+                ("pairs_full_table_fallback", ctypes.c_int64), ("points_partial", ctypes.c_int64),
+                ("node_evals_list64", ctypes.c_int64), ("pairs_list64", ctypes.c_int64),
+                ("pairs_full_table_list64", ctypes.c_int64)]
 
 
 class _ServerStats(ctypes.Structure):
@@ -71,7 +73,8 @@ class _PipePeaks(ctypes.Structure):
     _fields_ = [("dfma_per_s", ctypes.c_double), ("dmul_per_s", ctypes.c_double),
                 ("dadd_per_s", ctypes.c_double), ("ffma_per_s", ctypes.c_double),
                 ("rcp32_per_s", ctypes.c_double), ("sm_count", ctypes.c_int),
-                ("dfma_mhz", ctypes.c_double), ("ffma_mhz", ctypes.c_double)]
+                ("dfma_mhz", ctypes.c_double), ("ffma_mhz", ctypes.c_double),
+                ("fp64_mix_per_s", ctypes.c_double)]
 
 
 class _RequestInfo(ctypes.Structure):
@@ -306,15 +309,17 @@ class EvalStats:
     pairs_fallback: int = 0
     pairs_full_table: int = 0
     pairs_full_table_fallback: int = 0
+    points_partial: int = 0
+    node_evals_list64: int = 0
+    pairs_list64: int = 0
+    pairs_full_table_list64: int = 0
 
 
 def last_stats() -> EvalStats:
     lib = load_library()
     s = _EvalStats()
     _check(lib.gfc_last_stats(ctypes.byref(s)), "gfc_last_stats")
-    return EvalStats(s.points, s.points_fp64, s.node_evals, s.kernel_launches, s.pairs_evaluated,
-                     s.node_evals_fallback, s.pairs_fallback, s.pairs_full_table,
-                     s.pairs_full_table_fallback)
+    return EvalStats(*(getattr(s, k) for k, _ in _EvalStats._fields_))
 
 
 def version():
@@ -336,7 +341,7 @@ def measure_pipe_peaks(seconds: float = 0.2, stream=None) -> dict:
            "gfc_measure_pipe_peaks")
     return {"dfma_per_s": p.dfma_per_s, "dmul_per_s": p.dmul_per_s, "dadd_per_s": p.dadd_per_s,
             "ffma_per_s": p.ffma_per_s, "rcp32_per_s": p.rcp32_per_s, "sm_count": p.sm_count,
-            "dfma_mhz": p.dfma_mhz, "ffma_mhz": p.ffma_mhz}
+            "dfma_mhz": p.dfma_mhz, "ffma_mhz": p.ffma_mhz, "fp64_mix_per_s": p.fp64_mix_per_s}
 
 
 # --------------------------------------------------------------------------

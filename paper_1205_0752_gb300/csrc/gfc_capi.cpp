@@ -151,6 +151,7 @@ struct Tables {
     int n_r, n_a, dim, ang_rule;
     double L;
     double2 *rad64 = nullptr, *seg64 = nullptr, *arc64 = nullptr;
+    double2 *rayp64 = nullptr;   // (rho^2, rho^(D-1) W) of the radial nodes
     float2 *rad32 = nullptr, *seg32 = nullptr, *arc32 = nullptr;
     float4 *rad_df = nullptr, *seg_df = nullptr, *arc_df = nullptr;
     double2 *tail64 = nullptr;
@@ -375,12 +376,12 @@ static void build_rules(Tables &T, std::vector<double> &r64, std::vector<float4>
 
 // Per (device, stream) scratch: calls on one stream are ordered by the
 // stream, so they can share it; calls on different streams get their own.
-// counters: [0] work counter of the first launch, [1] of the second, [2]
-// length of the fallback list, [3] node-evaluation count and [4] angular
-// pairs evaluated by the first launch, [5] pairs and [6] node evaluations of
-// the fallback launch (mixed precision), [7] and [8] the pairs of the first
-// and the fallback launch that were the full table's; the G0(mu2) kernel of
-// every call zeroes them.
+// counters: [0] work counter of the first launch, [1] of the node-group
+// launch and [9] of the binary64 list launch (mixed precision), [2] length of
+// the binary64 list and [10] of the node list, [3] node evaluations, [4]
+// angular pairs and [7] full-table pairs of the first launch, [6], [5] and
+// [8] the same of the node-group launch, [12], [11] and [13] of the binary64
+// list launch; the G0(mu2) kernel of every call zeroes them.
 struct Scratch {
     double *partials = nullptr;   // 2 * kMaxG0Warps
     unsigned *ticket = nullptr;
@@ -388,6 +389,10 @@ struct Scratch {
     unsigned long long *counters = nullptr;   // kCounters
     int64_t *list = nullptr;      // binary64 list of the mixed precision
     int64_t list_cap = 0;
+    NodeEntry *node_list = nullptr;   // partially routed points of the mixed precision
+    int64_t node_list_cap = 0;
+    float4 *snap = nullptr;       // the binary32 bulk's group snapshots
+    int64_t snap_slots = 0;
     double *stage_x = nullptr, *stage_G = nullptr;   // host-path staging
     int64_t stage_cap = 0;
 };
@@ -413,6 +418,7 @@ static std::map<int, DeviceState> g_dev;
 static int free_tables(Tables &T)
 {
     cudaFree(T.rad64);
+    cudaFree(T.rayp64);
     cudaFree(T.seg64);
     cudaFree(T.arc64);
     cudaFree(T.rad32);
@@ -541,7 +547,7 @@ static int build_tables(Tables &T)
     std::vector<double> gx, gw;
     // radial: t = (1 + xi)/2 on (0, 1), |q| = L t/(1 - t), W = L/(1 - t)^2 w/2
     gauss_legendre(T.n_r, gx, gw);
-    std::vector<double2> rad64(T.n_r);
+    std::vector<double2> rad64(T.n_r), rayp64(T.n_r);
     std::vector<float2> rad32(T.n_r);
     for (int k = 0; k < T.n_r; ++k) {
         // 1 - t = (1 - xi)/2 computed without cancellation from the angle form
@@ -549,6 +555,10 @@ static int build_tables(Tables &T)
         double rho = T.L * t / omt, W = T.L / (omt * omt) * 0.5 * gw[k];
         rad64[k] = make_double2(rho, W);
         rad32[k] = make_float2((float)rho, (float)W);
+        // the binary64 ray node's rho^2 and measure rho^(D-1) W, rounded as
+        // the kernels would round them
+        const double r2 = rho * rho;
+        rayp64[k] = make_double2(r2, (T.dim == 4 ? r2 * rho : r2) * W);
     }
     // the clustered rule's tail: n_r/2 GL nodes on the same mapped half-line
     gauss_legendre(T.n_r / 2, gx, gw);
@@ -595,6 +605,7 @@ static int build_tables(Tables &T)
     for (size_t j = 0; j < r64.size(); ++j) rulesD[j] = dfv(r64[j]);
     int st;
     if ((st = upload(&T.rad64, rad64, T.bytes)) || (st = upload(&T.rad32, rad32, T.bytes)) ||
+        (st = upload(&T.rayp64, rayp64, T.bytes)) ||
         (st = upload(&T.seg64, seg64, T.bytes)) || (st = upload(&T.seg32, seg32, T.bytes)) ||
         (st = upload(&T.arc64, arc64, T.bytes)) || (st = upload(&T.arc32, arc32, T.bytes)) ||
         (st = upload(&T.ang64, ang64, T.bytes)) || (st = upload(&T.ang32, ang32, T.bytes)) ||
@@ -761,6 +772,7 @@ static void fill_kparams_tables(KParams &kp, const gfc_params *p, const Tables &
     kp.npair = npair_of(p);
     kp.ang_exact = p->angular_rule == GFC_ANG_EXACT;
     kp.rad64 = T.rad64;
+    kp.rayp64 = T.rayp64;
     kp.rad32 = T.rad32;
     kp.seg64 = T.seg64;
     kp.seg32 = T.seg32;
@@ -832,6 +844,31 @@ static int grow_list(Scratch &S, int64_t n)
     return GFC_OK;
 }
 
+// The node list (one entry per point at most) and the bulk's snapshots: one
+// slot of kMaxGroups x 32 float4 per warp the binary32 bulk can have resident
+// (every SM at 8 blocks of 256 threads, the most 2048 threads allow).
+static int grow_partial(Scratch &S, int64_t n)
+{
+    if (S.node_list_cap < n) {
+        cudaFree(S.node_list);
+        S.node_list = nullptr;
+        S.node_list_cap = 0;
+        cudaError_t e = dev_malloc((void **)&S.node_list, sizeof(NodeEntry) * (n > 0 ? n : 1));
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(node list)");
+        S.node_list_cap = n;
+    }
+    if (!S.snap) {
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        const int64_t slots = (int64_t)(sms > 0 ? sms : 1) * 8 * 8;
+        cudaError_t e = dev_malloc((void **)&S.snap, sizeof(float4) * kMaxGroups * 32 * slots);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(group snapshots)");
+        S.snap_slots = slots;
+    }
+    return GFC_OK;
+}
+
 static DevTables dev_tables(const Tables &T)
 {
     DevTables tb;
@@ -861,7 +898,9 @@ static int run(const gfc_propagator *prop, const gfc_params *p, KParams kp_point
         return rc;
     Scratch *S;
     if ((rc = get_scratch(dev, st, &S))) return rc;
-    if (p->precision == GFC_MIXED && (rc = grow_list(*S, kp_points.npts))) return rc;
+    if (p->precision == GFC_MIXED &&
+        ((rc = grow_list(*S, kp_points.npts)) || (rc = grow_partial(*S, kp_points.npts))))
+        return rc;
     KParams kp;
     fill_kparams(kp, p, *T, pc, *S);
     kp.cond_out = cond_out;
@@ -892,19 +931,34 @@ static int run(const gfc_propagator *prop, const gfc_params *p, KParams kp_point
             if (e != cudaSuccess) return cuda_fail(e, "eval launch");
             stats.kernel_launches += 1;
         } else {
+            // the binary32 bulk; points it routes go whole (cut band, pinch)
+            // to the binary64 list or with their worst node groups to the
+            // node list
             kp.mode = MODE_BULK32;
             kp.counter = S->counters;
+            kp.node_list = S->node_list;
+            kp.node_list_count = S->counters + 10;
+            kp.snap = S->snap;
+            kp.snap_slots = S->snap_slots;
             e = launch_eval(kp, tb, ARITH_F32, st);
             if (e != cudaSuccess) return cuda_fail(e, "eval launch (binary32)");
-            kp.mode = MODE_LIST64;
+            // the node groups in the fallback arithmetic, counted apart
+            kp.mode = MODE_NODES;
             kp.counter = S->counters + 1;
-            // the fallback launch counts its work apart from the binary32 bulk
             kp.pair_count = S->counters + 5;
             kp.node_count = S->counters + 6;
             kp.pair_full_count = S->counters + 8;
             e = launch_eval(kp, tb, p->mixed_fallback == GFC_F32X2 ? ARITH_DF : ARITH_F64, st);
+            if (e != cudaSuccess) return cuda_fail(e, "eval launch (node groups)");
+            // the whole points in binary64
+            kp.mode = MODE_LIST64;
+            kp.counter = S->counters + 9;
+            kp.pair_count = S->counters + 11;
+            kp.node_count = S->counters + 12;
+            kp.pair_full_count = S->counters + 13;
+            e = launch_eval(kp, tb, ARITH_F64, st);
             if (e != cudaSuccess) return cuda_fail(e, "eval launch (binary64 list)");
-            stats.kernel_launches += 2;
+            stats.kernel_launches += 3;
         }
     }
     stats.points_fp64 = p->precision != GFC_MIXED ? kp.npts : -1;
@@ -1141,13 +1195,19 @@ int gfc_last_stats(gfc_eval_stats *out)
         if (e == cudaSuccess)
             e = cudaMemcpy(c, g_last_call.counters, sizeof c, cudaMemcpyDeviceToHost);
         if (e != cudaSuccess) return cuda_fail(e, "reading the call's counters");
-        out->node_evals = (int64_t)(c[3] + c[6]);
-        out->pairs_evaluated = (int64_t)(c[4] + c[5]);
+        out->node_evals = (int64_t)(c[3] + c[6] + c[12]);
+        out->pairs_evaluated = (int64_t)(c[4] + c[5] + c[11]);
+        out->pairs_full_table = (int64_t)(c[7] + c[8] + c[13]);
         out->node_evals_fallback = (int64_t)c[6];
         out->pairs_fallback = (int64_t)c[5];
-        out->pairs_full_table = (int64_t)(c[7] + c[8]);
         out->pairs_full_table_fallback = (int64_t)c[8];
-        if (g_last_call.precision == GFC_MIXED) out->points_fp64 = (int64_t)c[2];
+        out->node_evals_list64 = (int64_t)c[12];
+        out->pairs_list64 = (int64_t)c[11];
+        out->pairs_full_table_list64 = (int64_t)c[13];
+        if (g_last_call.precision == GFC_MIXED) {
+            out->points_fp64 = (int64_t)c[2];
+            out->points_partial = (int64_t)c[10];
+        }
     }
     return GFC_OK;
 }
@@ -1167,6 +1227,8 @@ int gfc_release(void)
         cudaFree(S.ticket);
         cudaFree(S.g0mu);
         cudaFree(S.counters);
+        cudaFree(S.node_list);
+        cudaFree(S.snap);
         cudaFree(S.list);
         cudaFree(S.stage_x);
         cudaFree(S.stage_G);

@@ -12,14 +12,38 @@ namespace gfc {
 // The closed-form angle and the clustered radial rule have variant kernels of
 // their own, with the generic pair loop only (NP = 0): the dispatch sends
 // them here.
+// The kernel kind of a launch (see eval_loop): 1 the node groups of the
+// mixed precision's partial routing (binary64 and double-float), 2 the
+// binary32 bulk that records them, else 0.
+template <typename T>
+static int launch_kind(const KParams &kp)
+{
+    if constexpr (std::is_same<T, float>::value)
+        return kp.mode == MODE_BULK32 && kp.node_list && kp.mixed_rtol > 0.0 ? 2 : 0;
+    else
+        return kp.mode == MODE_NODES ? 1 : 0;
+}
+
+template <typename T, int NP, int CL>
+static cudaError_t eval_kind(const KParams &kp, const DevTables &tb, cudaStream_t st)
+{
+    const bool two = kp.pc.kind == 2;
+    const int k = launch_kind<T>(kp);
+    if constexpr (std::is_same<T, float>::value) {
+        if (k == 2) return two ? run_eval<T, NP, 2, CL, 2>(kp, tb, st) : run_eval<T, NP, 1, CL, 2>(kp, tb, st);
+    } else {
+        if (k == 1) return two ? run_eval<T, NP, 2, CL, 1>(kp, tb, st) : run_eval<T, NP, 1, CL, 1>(kp, tb, st);
+    }
+    return two ? run_eval<T, NP, 2, CL>(kp, tb, st) : run_eval<T, NP, 1, CL>(kp, tb, st);
+}
+
 template <typename T, int NP>
 cudaError_t eval_inst(const KParams &kp, const DevTables &tb, cudaStream_t st)
 {
     if constexpr (NP == 0) {
-        if (kp.radial_rule == 1 || kp.ang_exact)
-            return kp.pc.kind == 2 ? run_eval<T, 0, 2, 1>(kp, tb, st) : run_eval<T, 0, 1, 1>(kp, tb, st);
+        if (kp.radial_rule == 1 || kp.ang_exact) return eval_kind<T, 0, 1>(kp, tb, st);
     }
-    return kp.pc.kind == 2 ? run_eval<T, NP, 2, 0>(kp, tb, st) : run_eval<T, NP, 1, 0>(kp, tb, st);
+    return eval_kind<T, NP, 0>(kp, tb, st);
 }
 
 template <typename T, int NP>

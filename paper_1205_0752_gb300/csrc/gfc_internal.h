@@ -12,7 +12,7 @@ constexpr int kMaxRadial = 16384;
 constexpr int kMaxAngular = 512;
 constexpr int kMaxPairs = kMaxAngular / 2;
 constexpr int kMaxRules = 32;
-constexpr int kCounters = 12;  // per-call device counters (see gfc_capi.cpp)
+constexpr int kCounters = 16;  // per-call device counters (see gfc_capi.cpp)
 
 // Contour of one pass of a point (Step 3, eq. 15).
 enum PassKind : int { PASS_RAY = 0, PASS_DETOUR = 1 };
@@ -23,8 +23,22 @@ enum LaunchMode : int {
     MODE_BULK32 = 1,     // mixed, binary32: every point not in the binary64
                          // band; band points and points whose estimated
                          // rounding error exceeds mixed_rtol go to the list
-    MODE_LIST64 = 2      // mixed, binary64: the points of the list
+    MODE_LIST64 = 2,     // mixed, binary64: the points of the list
+    MODE_NODES = 3       // mixed: the node groups of the partially routed
+                         // points (node_list), added to the bulk's G
 };
+
+// A partially routed point of the mixed precision: the binary32 bulk wrote
+// the sum of its kept node groups; the groups in `mask` (bit g: the point's
+// iterations [g gsz, (g + 1) gsz), an iteration being 32 consecutive nodes of
+// a pass, numbered across the passes) are re-evaluated in the fallback
+// arithmetic and added.
+struct NodeEntry {
+    int64_t point;
+    unsigned mask;
+    int gsz;
+};
+constexpr int kMaxGroups = 32;
 
 // Per-propagator constants prepared on the host in FP64. Poles y_p are the
 // zeros of the leg denominators in the y = q^2 plane.
@@ -68,6 +82,7 @@ struct KParams {
     double *G;           // interleaved complex128 output
     // node tables (device, FP64 and FP32 copies)
     const double2 *rad64;   // (rho_k, W_k)
+    const double2 *rayp64;  // (rho_k^2, rho_k^(D-1) W_k): binary64 ray nodes from q = 0
     const float2 *rad32;
     const double2 *seg64;   // (t_k, w_k) on [0, 1]
     const float2 *seg32;
@@ -85,8 +100,14 @@ struct KParams {
     // mixed-precision routing
     double cut_band, pinch_angle;
     double mixed_rtol;           // a-posteriori routing threshold (0: off)
-    int64_t *list;               // points routed to binary64
+    int64_t *list;               // points routed whole to the list arithmetic
     unsigned long long *list_count;
+    // partial routing (one-shot calls; null in the server, whose routed
+    // points go whole to `list`): node groups re-evaluated in the fallback
+    NodeEntry *node_list;
+    unsigned long long *node_list_count;
+    float4 *snap;                // per warp slot [group][lane]: running sums at group ends
+    int64_t snap_slots;          // warp slots of `snap`
     double *cond_out;            // optional per-point K_D sum_k M_k
     // compressed angular rules: Gauss rules of the discrete measure
     // sum_j e_j delta(t - t_j) with rule_n[r] nodes; rule r reproduces the full

@@ -41,6 +41,13 @@ namespace gfc {
 // the nodes' error scale), from binary32-vs-FP64 runs over the test grids
 constexpr double kMixedErrFactor = 2.0;
 constexpr float kMixedPinchQ = 1e-5f;   // |1 - w t|^2 below which a point is routed
+// partial routing: the kept node groups' error estimate must pass with this
+// margin (the estimate's spread around the error is wider once the largest
+// groups are gone)
+#ifndef GFC_PARTIAL_MARGIN
+#define GFC_PARTIAL_MARGIN 4.0
+#endif
+constexpr double kPartialMargin = GFC_PARTIAL_MARGIN;
 // weight of the pole terms of kappa on binary32 ray nodes with y exact
 #ifndef GFC_POLE_WEIGHT
 #define GFC_POLE_WEIGHT 0.5
@@ -381,15 +388,26 @@ __device__ __forceinline__ Node<T> ray_node_at(const KParams &kp, T rho, T W, C<
     return n;
 }
 
-// node k of the mapped ray from q = 0
+// node k of the mapped ray from q = 0 (binary64: rho^2 and the measure
+// rho^(D-1) W from the table, rounded there as ray_node_at rounds them)
 template <typename T>
 __device__ __forceinline__ Node<T> ray_node(const KParams &kp, int k, C<T> e2, C<T> eD)
 {
-    T rho, W;
-    load2<T>(kp, 0, k, rho, W);
-    Node<T> n = ray_node_at<T>(kp, rho, W, e2, eD);
-    n.ylo = {T(0), T(0)};
-    return n;
+    if constexpr (std::is_same<T, double>::value) {
+        const double2 v = __ldg(kp.rayp64 + k);
+        Node<T> n;
+        n.y = v.x * e2;
+        n.sc = 1.0;
+        n.Jt = v.y * eD;
+        n.ylo = {0.0, 0.0};
+        return n;
+    } else {
+        T rho, W;
+        load2<T>(kp, 0, k, rho, W);
+        Node<T> n = ray_node_at<T>(kp, rho, W, e2, eD);
+        n.ylo = {T(0), T(0)};
+        return n;
+    }
 }
 
 // node k of the mapped ray from |q| = rho0 > 0 (the tail of a detour)
@@ -411,7 +429,7 @@ __device__ __forceinline__ Node<T> ray_node_from(const KParams &kp, int k, C<T> 
 // each (the contour passes close to y = -M2 next to the negative real axis,
 // where y + M2 cancels).
 __device__ __forceinline__ Node<float> ray_node_exact_y(const KParams &kp, int k, C<float> e2,
-                                                        C<float> eD)
+                                                        C<float> eD, C<float> e2lo = {0.0f, 0.0f})
 {
     const float4 v = __ldg(kp.rad_df + k);
     const float rh = v.x, rl = v.y, W = v.z;
@@ -420,8 +438,10 @@ __device__ __forceinline__ Node<float> ray_node_exact_y(const KParams &kp, int k
     Node<float> n;
     n.y.r = p * e2.r;
     n.y.i = p * e2.i;
-    n.ylo.r = fmaf(p, e2.r, -n.y.r) + pe * e2.r;
-    n.ylo.i = fmaf(p, e2.i, -n.y.i) + pe * e2.i;
+    // (with e2lo, the ray direction's own remainder: the ray of the exact
+    // direction x/|x|, not of its binary32 rounding)
+    n.ylo.r = fmaf(p, e2lo.r, fmaf(p, e2.r, -n.y.r) + pe * e2.r);
+    n.ylo.i = fmaf(p, e2lo.i, fmaf(p, e2.i, -n.y.i) + pe * e2.i);
     n.sc = 1.0f + p;
     float s = rcp(n.sc);
     s = s * s;
@@ -878,17 +898,20 @@ struct PassPre {
     C<T> omx[NT];     // Omega (x + M2_t)
     int full[NT];     // k-leg is the whole dressed propagator
     int same[NT];     // k-leg and (p-k)-leg share the pole: one reciprocal
-    C<T> xm[NT], xml[NT];   // binary32: x + M2_t rounded, and its remainder (TwoSum)
+    C<T> xm[NT], xml[NT];   // x + M2_t rounded (binary32: and its remainder, TwoSum)
+    C<T> x4;                // 4 x
+    C<T> omxl[NT];          // binary32: Omega (x + M2_t) - omx (the product in binary64)
 };
 
 
 
-template <typename T, int NT>
+template <typename T, int NT, int ACC = 0>
 __device__ __forceinline__ PassPre<T, NT> pass_pre(const KParams &kp, const Plan<T> &P, int pass,
                                                    C<T> x)
 {
     PassPre<T, NT> pp;
     pp.nt = P.nterm[pass];
+    pp.x4 = T(4) * x;
     const T Om = T(kp.Omega);
 #pragma unroll
     for (int s = 0; s < NT; ++s) {
@@ -896,9 +919,17 @@ __device__ __forceinline__ PassPre<T, NT> pass_pre(const KParams &kp, const Plan
         pp.m2q[s] = tm.m2q;
         pp.m2k[s] = tm.m2k;
         pp.cx2[s] = tm.c * (T(2) * x);
-        pp.omx[s] = Om * (x + tm.m2q);
+        if constexpr (!(std::is_same<T, float>::value && ACC)) pp.omx[s] = Om * (x + tm.m2q);
         pp.full[s] = tm.full;
         pp.same[s] = !tm.full && tm.m2k.r == tm.m2q.r && tm.m2k.i == tm.m2q.i;
+        if constexpr (std::is_same<T, float>::value && ACC) {
+            // Omega (x + M2) to double-float accuracy: rounded once per pass it
+            // would shift every node's leading term alike (see node_value)
+            const double orr = kp.Omega * ((double)x.r + (double)tm.m2q.r);
+            const double oii = kp.Omega * ((double)x.i + (double)tm.m2q.i);
+            pp.omx[s] = {(float)orr, (float)oii};
+            pp.omxl[s] = {(float)(orr - (double)pp.omx[s].r), (float)(oii - (double)pp.omx[s].i)};
+        }
         if constexpr (std::is_same<T, float>::value) {
             // TwoSum (Knuth): x + M2 = xm + xml exactly
             const C<T> m = tm.m2q;
@@ -939,7 +970,7 @@ __device__ __forceinline__ df trsqrt(df x) { return df(rsqrtf(x.hi), 0.0f); }
 // inputs: |y|/|y + M2| per propagator factor (the contour passes near a pole
 // when arg x is near pi), (|x| + |y|)/|a| for the denominator a, and
 // |w|/|1 - w t|_min for the angular sum next to a pinch (binary32 only).
-template <typename T, int NP, int NT, int V, int FC = 0>
+template <typename T, int NP, int NT, int V, int FC = 0, int ACC = 0>
 __device__ __forceinline__ C<T> node_value(const KParams &kp, const AngTab<T, tab_size<NP>()> &tab,
                                            const T *stab, const void *srules,
                                            const PassPre<T, NT> &pp, C<T> x, const Node<T> &nd,
@@ -960,7 +991,8 @@ __device__ __forceinline__ C<T> node_value(const KParams &kp, const AngTab<T, ta
     // double-float has no error-scale output (it would cost registers)
     const bool want_mag = std::is_same<T, float>::value ||
                           (std::is_same<T, double>::value && kp.cond_out != nullptr);
-    C<T> ia[NT], v[NT], w[NT];
+    // u = y/a (v = 4u), w = 4xy/a^2
+    C<T> ia[NT], u[NT], w[NT];
     T kap[NT];
 #pragma unroll
     for (int s = 0; s < NT; ++s) {
@@ -971,8 +1003,14 @@ __device__ __forceinline__ C<T> node_value(const KParams &kp, const AngTab<T, ta
         else
             a = x + nd.y + pp.m2q[s];
         ia[s] = cinv(a);
-        v[s] = T(4) * (nd.y * ia[s]);
-        w[s] = (x * v[s]) * ia[s];
+        if constexpr (f32) {
+            // binary32 keeps v = 4u itself (its registers are the scarcer)
+            u[s] = T(4) * (nd.y * ia[s]);
+            w[s] = (x * u[s]) * ia[s];
+        } else {
+            u[s] = nd.y * ia[s];
+            w[s] = (pp.x4 * u[s]) * ia[s];
+        }
         if (want_mag) kap[s] = (cabs1(x) + cabs1(nd.y)) * rcp(cabs1(a));
     }
     T A[NT], B[NT];
@@ -981,7 +1019,7 @@ __device__ __forceinline__ C<T> node_value(const KParams &kp, const AngTab<T, ta
         qmin = T(1e30);
 #pragma unroll
         for (int s = 0; s < NT; ++s) {
-            Sx[s] = exact_S<T>(kp.dim, v[s], w[s]);
+            Sx[s] = exact_S<T>(kp.dim, f32 ? u[s] : T(4) * u[s], w[s]);
             if (sizeof(T) == 4) qmin = fmin(qmin, cabs2(C<T>{T(1) - w[s].r, -w[s].i}));
             A[s] = B[s] = T(0);
         }
@@ -1000,8 +1038,26 @@ __device__ __forceinline__ C<T> node_value(const KParams &kp, const AngTab<T, ta
             S = Sx[s];
         } else {
             C<T> T2 = {A[s] - w[s].r * B[s], w[s].i * B[s]};
-            C<T> lead = (del * nd.y - pp.omx[s]) * ia[s] - Om1 * w[s];
-            C<T> vw = (v[s] - w[s]) * w[s];
+            C<T> lead;
+            if constexpr (f32 && ACC) {
+                // the leading term with its constants delta, Omega1 and
+                // Omega (x + M2) to double-float accuracy (low parts from the
+                // double-float copies): rounded to binary32 they would shift
+                // every node's leading term alike, an error that cancels in a
+                // sum over all nodes but not when some of them are evaluated
+                // again in another arithmetic (partial routing)
+                const float dl = kp.dfc[3], o1l = kp.dfc[1];
+                const C<T> dy = {fmaf(del, nd.y.r, dl * nd.y.r), fmaf(del, nd.y.i, dl * nd.y.i)};
+                const C<T> tt = {(dy.r - pp.omx[s].r) - pp.omxl[s].r, (dy.i - pp.omx[s].i) - pp.omxl[s].i};
+                const C<T> ow = {fmaf(Om1, w[s].r, o1l * w[s].r), fmaf(Om1, w[s].i, o1l * w[s].i)};
+                lead = tt * ia[s] - ow;
+            } else {
+                lead = (del * nd.y - pp.omx[s]) * ia[s] - Om1 * w[s];
+            }
+            // (v - w) w, v - w = 4u - w with one rounding
+            const C<T> vmw = f32 ? u[s] - w[s]
+                                 : C<T>{fma(T(4), u[s].r, -w[s].r), fma(T(4), u[s].i, -w[s].i)};
+            const C<T> vw = vmw * w[s];
             S = lead + vw * T2;
         }
         // P1(y) / (y + M2), times (1 + |y|)^2 where the node is scaled
@@ -1114,17 +1170,54 @@ __device__ __forceinline__ void point_x(const KParams &kp, int64_t p, double &xr
     }
 }
 
-// One pass of a point's contour, the lane's share of its nodes. CL = 1 (the
-// variant kernels) compiles in the options that the default kernels leave
-// out so as to carry none of their registers: the closed-form angular
-// integral and the clustered radial rule.
-template <typename T, int NP, int NTT, int CL>
-__device__ __forceinline__ void run_pass(const KParams &kp, const AngTab<T, tab_size<NP>()> &tab,
-                                         const T *stab, const void *srules, const Plan<T> &P,
-                                         int pass, C<T> x, C<T> e2, C<T> eD, int lane, Acc<T> &acc,
-                                         ErrAcc<T> &ea, T &qall, int &pairs, int &pfull)
+// Node groups of a point's contour (mixed precision, partial routing): the
+// point's iterations -- 32 consecutive nodes of a pass, one per lane --
+// numbered across its passes, gsz iterations per group, at most kMaxGroups
+// groups. `mask` (0: all) selects the groups a launch evaluates; with `snap`
+// set (the binary32 bulk), every group end records each lane's running
+// compensated sum in snap[group][lane] and the warp's error scale of the
+// group in gerr[group].
+struct Groups {
+    unsigned mask;
+    int gsz, ngroups;
+    float4 *snap;
+    float2 *gerr;
+};
+// position of a lane's loop in the groups
+struct GroupCursor {
+    int g, left;   // current group; iterations left in it
+};
+
+// the warp's (sum M, sum (M kappa)^2) of the group just ended, stored by lane 0
+__device__ __forceinline__ void group_end(const Groups &gr, int g, int lane, const Acc<float> &acc,
+                                          ErrAcc<float> &ea)
 {
-    const PassPre<T, NTT> pp = pass_pre<T, NTT>(kp, P, pass, x);
+    gr.snap[g * 32 + lane] = make_float4(acc.sr, acc.cr, acc.si, acc.ci);
+    float s1 = ea.s1, s2 = ea.s2;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+        s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+    }
+    if (lane == 0) gr.gerr[g] = make_float2(s1, s2);
+    ea.s1 = ea.s2 = 0.0f;
+}
+
+// One pass of a point's contour, the lane's share of its nodes (those of
+// the groups the mask selects). CL = 1 (the variant kernels) compiles in the
+// options that the default kernels leave out so as to carry none of their
+// registers: the closed-form angular integral and the clustered radial rule.
+// Returns the nodes of the pass the warp evaluated. GM selects the group
+// handling at compile time: 0 none (every node), 1 the groups of gr.mask,
+// 2 every node with the binary32 bulk's group records.
+template <typename T, int NP, int NTT, int CL, int GM = 0>
+__device__ __forceinline__ int run_pass(const KParams &kp, const AngTab<T, tab_size<NP>()> &tab,
+                                        const T *stab, const void *srules, const Plan<T> &P,
+                                        int pass, C<T> x, C<T> e2, C<T> eD, int lane, Acc<T> &acc,
+                                        ErrAcc<T> &ea, T &qall, int &pairs, int &pfull,
+                                        const Groups &gr, GroupCursor &cur, C<T> e2lo)
+{
+    const PassPre<T, NTT> pp = pass_pre<T, NTT, (GM == 2 ? 1 : 0)>(kp, P, pass, x);
     const bool ray = P.kind[pass] == PASS_RAY;
     const int nn = ray ? kp.n_r : 3 * kp.n_s + kp.n_r;
     DetourPre<T> *dps = detour_slot<T>();
@@ -1140,57 +1233,103 @@ __device__ __forceinline__ void run_pass(const KParams &kp, const AngTab<T, tab_
     // it per node, where its compensated sum and error scale were set up)
     constexpr int FC = (NTT == 1 && !std::is_same<T, float>::value) ? 1 : 0;
     C<T> ps = {T(0), T(0)};
-    for (int k = lane; k < nn; k += 32) {
-        Node<T> nd;
-        if (!ray)
-            nd = detour_node<T>(kp, k, e2, eD, *dps);
-        else if (CL && P.clus)
-            nd = ray_node_cl<T>(kp, k, e2, eD, P.cl_c, P.cl_d, P.cl_eta);
-        else if constexpr (std::is_same<T, float>::value)
-            nd = ray_node_exact_y(kp, k, e2, eD);
-        else
-            nd = ray_node<T>(kp, k, e2, eD);
-        T qm;
-        int np;
-        C<T> v = node_value<T, NP, NTT, CL, FC>(kp, tab, stab, srules, pp, x, nd, ea, qm, np,
-                                                exact_y);
-        if constexpr (FC) ps = ps + v;
-        else acc_add(acc, v);
-        qall = fmin(qall, qm);
-        if (np < 0) {
-            pfull -= np;
-            pairs -= np;
-        } else {
-            pairs += np;
+    int evaluated = 0;
+    auto node = [&](int k) {
+                Node<T> nd;
+                if (!ray)
+                    nd = detour_node<T>(kp, k, e2, eD, *dps);
+                else if (CL && P.clus)
+                    nd = ray_node_cl<T>(kp, k, e2, eD, P.cl_c, P.cl_d, P.cl_eta);
+                else if constexpr (std::is_same<T, float>::value)
+                    nd = GM == 2 ? ray_node_exact_y(kp, k, e2, eD, e2lo) : ray_node_exact_y(kp, k, e2, eD);
+                else
+                    nd = ray_node<T>(kp, k, e2, eD);
+                T qm;
+                int np;
+                C<T> v = node_value<T, NP, NTT, CL, FC, (GM == 2 ? 1 : 0)>(kp, tab, stab, srules, pp,
+                                                                           x, nd, ea, qm, np, exact_y);
+                if constexpr (FC) ps = ps + v;
+                else acc_add(acc, v);
+                qall = fmin(qall, qm);
+                if (np < 0) {
+                    pfull -= np;
+                    pairs -= np;
+                } else {
+                    pairs += np;
+                }
+    };
+    if constexpr (GM == 0) {
+        for (int k = lane; k < nn; k += 32) node(k);
+        evaluated = nn;
+    } else {
+        for (int base = 0; base < nn; base += 32) {
+            // warp-uniform: the group of this iteration is selected
+            if (GM == 2 || (cur.g < kMaxGroups && ((gr.mask >> cur.g) & 1u))) {
+                evaluated += min(32, nn - base);
+                if (base + lane < nn) node(base + lane);
+            }
+            if (--cur.left == 0) {
+                if constexpr (GM == 2 && std::is_same<T, float>::value)
+                    group_end(gr, cur.g, lane, acc, ea);
+                cur.left = gr.gsz;
+                ++cur.g;
+            }
         }
     }
     if constexpr (FC) acc_add(acc, pp.cx2[0] * ps);
+    return evaluated;
 }
 
-// Sum over one point's contour, per lane, into acc; returns the point's
-// number of contour nodes.
-template <typename T, int NP, int NT, int CL>
+// Sum over one point's contour (the groups gr.mask selects), per lane, into
+// acc; returns the number of contour nodes evaluated. With gr.snap set (the
+// binary32 bulk with partial routing) it first sizes the groups: the fewest
+// iterations per group that give at most kMaxGroups groups.
+template <typename T, int NP, int NT, int CL, int GM = 0>
 __device__ __forceinline__ int point_sum(const KParams &kp, const AngTab<T, tab_size<NP>()> &tab,
                                          const T *stab, const void *srules, double xr, double xi,
                                          int lane, Acc<T> &acc, ErrAcc<T> &ea, T &qall,
-                                         int &pairs, int &pfull)
+                                         int &pairs, int &pfull, Groups &gr)
 {
     const Plan<T> P = make_plan<T, CL>(kp, xr, xi);
     const C<T> x = cvt<T>(xr, xi);
     // e^{i D theta} of the ray, once per point
-    const C<T> e2 = P.eth * P.eth;
+    C<T> e2 = P.eth * P.eth;
+    C<T> e2lo = {T(0), T(0)};
+    if constexpr (GM == 2) {
+        // the binary32 bulk with partial routing puts its ray nodes on the
+        // exact direction x/|x| (binary32 value and remainder): the node
+        // groups evaluated again in the fallback arithmetic lie on that ray,
+        // and a ray turned by the direction's rounding would change the
+        // kept groups' sum coherently
+        const double ax = sqrt(xr * xr + xi * xi);
+        const double dr = xr / ax, di = xi / ax;
+        e2 = {(float)dr, (float)di};
+        e2lo = {(float)(dr - (double)e2.r), (float)(di - (double)e2.i)};
+    }
     const C<T> eD = kp.dim == 4 ? e2 * e2 : e2 * P.eth;
+    if (GM == 2) {
+        int iters = 0;
+        for (int pass = 0; pass < P.npass; ++pass)
+            iters += ((P.kind[pass] == PASS_RAY ? kp.n_r : 3 * kp.n_s + kp.n_r) + 31) / 32;
+        gr.gsz = (iters + kMaxGroups - 1) / kMaxGroups;
+        gr.ngroups = (iters + gr.gsz - 1) / gr.gsz;
+    }
+    GroupCursor cur = {0, gr.gsz};
     int total = 0;
 #pragma unroll
     for (int pass = 0; pass < 2; ++pass) {
         if (pass >= P.npass) break;
-        total += P.kind[pass] == PASS_RAY ? kp.n_r : 3 * kp.n_s + kp.n_r;
         if (NT > 1 && P.nterm[pass] == 2)
-            run_pass<T, NP, (NT > 1 ? 2 : 1), CL>(kp, tab, stab, srules, P, pass, x, e2, eD, lane,
-                                                 acc, ea, qall, pairs, pfull);
+            total += run_pass<T, NP, (NT > 1 ? 2 : 1), CL, GM>(kp, tab, stab, srules, P, pass, x, e2,
+                                                              eD, lane, acc, ea, qall, pairs, pfull,
+                                                              gr, cur, e2lo);
         else
-            run_pass<T, NP, 1, CL>(kp, tab, stab, srules, P, pass, x, e2, eD, lane, acc, ea, qall,
-                                   pairs, pfull);
+            total += run_pass<T, NP, 1, CL, GM>(kp, tab, stab, srules, P, pass, x, e2, eD, lane, acc,
+                                                ea, qall, pairs, pfull, gr, cur, e2lo);
+    }
+    if constexpr (std::is_same<T, float>::value) {
+        // the last group, if the iterations end inside it
+        if (GM == 2 && cur.left != gr.gsz) group_end(gr, cur.g, lane, acc, ea);
     }
     return total;
 }
@@ -1201,12 +1340,140 @@ __device__ __forceinline__ void list_append(const KParams &kp, int64_t p)
     kp.list[k] = p;
 }
 
+// compensated binary32 pairs (hi, lo) summed over the warp, TwoSum on the
+// high parts; every lane receives the sum
+__device__ __forceinline__ void warp_pair_sum(float &hr, float &lr, float &hi, float &li)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        float ohr = __shfl_xor_sync(0xffffffffu, hr, o), olr = __shfl_xor_sync(0xffffffffu, lr, o);
+        float ohi = __shfl_xor_sync(0xffffffffu, hi, o), oli = __shfl_xor_sync(0xffffffffu, li, o);
+        float cr = 0.0f, ci = 0.0f;
+        two_sum_add(hr, cr, ohr);
+        two_sum_add(hi, ci, ohi);
+        lr = lr + olr + cr;
+        li = li + oli + ci;
+    }
+}
+
+// A warp's per-group error scales of the binary32 bulk (shared memory, one
+// slot per warp of a block of 256)
+__device__ __forceinline__ float2 *group_err_slot()
+{
+    __shared__ float2 slots[8][kMaxGroups];
+    return slots[threadIdx.x >> 5];
+}
+
+// Epilogue of the binary32 bulk with partial routing. The point's rounding
+// error estimate is the one of the plain bulk (kMixedErrFactor 2^-24 E, E =
+// K_D (sqrt(sum (M kappa)^2) + sum M) over its nodes). A point that passes
+// keeps its binary32 value. A point next to a pinch goes whole to the
+// binary64 list. Otherwise the node groups with the largest share of E
+// (S1_g + sqrt(S2_g), S1_g = sum M and S2_g = sum (M kappa)^2 over group g)
+// are taken out one by one until the rest passes; the bulk writes the
+// compensated binary32 sum of the kept groups (each lane's running sum less
+// the removed groups' parts, from its snapshots at the group ends), and the
+// point goes to the node list with the mask of the removed groups, whose
+// nodes the fallback kernel evaluates and adds.
+__device__ __forceinline__ void bulk_partial_epilogue(const KParams &kp, int64_t p, int lane,
+                                                      const Acc<float> &acc, float qall,
+                                                      const Groups &gr, double *out)
+{
+    __syncwarp();
+    const float2 ge = lane < gr.ngroups ? gr.gerr[lane] : make_float2(0.0f, 0.0f);
+    float s1 = ge.x, s2 = ge.y;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+        s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+    }
+    float hr = acc.sr, lr = acc.cr, hi = acc.si, li = acc.ci;
+    warp_pair_sum(hr, lr, hi, li);
+    float qpt = qall;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) qpt = fminf(qpt, __shfl_xor_sync(0xffffffffu, qpt, o));
+    const double gr0 = kp.K_D * ((double)hr + (double)lr) - kp.g0mu[0];
+    const double gi0 = kp.K_D * ((double)hi + (double)li) - kp.g0mu[1];
+    // the largest sqrt(sum (M kappa)^2) + sum M that passes
+    const float lim = (float)(kp.mixed_rtol * sqrt(gr0 * gr0 + gi0 * gi0) /
+                              (kMixedErrFactor * 5.9604644775390625e-8 * kp.K_D));
+    if (!(kp.mixed_rtol > 0.0) || (sqrtf(s2) + s1 <= lim && !(qpt < kMixedPinchQ))) {
+        if (lane == 0) {
+            out[0] = gr0;
+            out[1] = gi0;
+            if (kp.cond_out) kp.cond_out[p] = kp.K_D * ((double)sqrtf(s2) + (double)s1);
+        }
+        __syncwarp();
+        return;
+    }
+    if (qpt < kMixedPinchQ) {
+        // next to a pinch no binary32 part is kept: every group goes to the
+        // fallback, which adds the whole sum to -G0(mu2)
+        if (lane == 0) {
+            out[0] = -kp.g0mu[0];
+            out[1] = -kp.g0mu[1];
+            if (kp.cond_out) kp.cond_out[p] = 0.0;
+            const unsigned long long k = atomicAdd(kp.node_list_count, 1ULL);
+            kp.node_list[k] = NodeEntry{p, gr.ngroups >= 32 ? 0xffffffffu : (1u << gr.ngroups) - 1u, gr.gsz};
+        }
+        __syncwarp();
+        return;
+    }
+    // take out the groups with the largest share, one per round (the same
+    // decision on every lane: the sums above are butterflies), until the rest
+    // passes with the margin kPartialMargin
+    const float S1 = ge.x, S2 = ge.y;
+    float score = lane < gr.ngroups ? S1 + sqrtf(S2) : -1.0f;
+    float r1 = s1, r2 = s2;
+    unsigned mask = 0u;
+    const float limk = lim * (float)(1.0 / kPartialMargin);
+    while (!(sqrtf(fmaxf(r2, 0.0f)) + fmaxf(r1, 0.0f) <= limk)) {
+        // non-negative binary32 values order as their bit patterns
+        const unsigned key = score >= 0.0f ? __float_as_uint(score) + 1u : 0u;
+        const unsigned mx = __reduce_max_sync(0xffffffffu, key);
+        if (mx == 0u) break;                       // every group is out
+        const int g = __ffs(__ballot_sync(0xffffffffu, key == mx)) - 1;
+        mask |= 1u << g;
+        r1 -= __shfl_sync(0xffffffffu, S1, g);
+        r2 -= __shfl_sync(0xffffffffu, S2, g);
+        if (lane == g) score = -1.0f;
+    }
+    // the lane's kept sum: its total less each removed group's part, the
+    // difference of its snapshots at the group's end and at the one before
+    float kr = acc.sr, klr = acc.cr, ki = acc.si, kli = acc.ci;
+    for (unsigned m = mask; m; m &= m - 1u) {
+        const int g = __ffs(m) - 1;
+        const float4 a = gr.snap[g * 32 + lane];
+        const float4 b = g > 0 ? gr.snap[(g - 1) * 32 + lane] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        two_sum_add(kr, klr, -a.x);
+        two_sum_add(kr, klr, b.x);
+        klr += b.y - a.y;
+        two_sum_add(ki, kli, -a.z);
+        two_sum_add(ki, kli, b.z);
+        kli += b.w - a.w;
+    }
+    warp_pair_sum(kr, klr, ki, kli);
+    if (lane == 0) {
+        out[0] = kp.K_D * ((double)kr + (double)klr) - kp.g0mu[0];
+        out[1] = kp.K_D * ((double)ki + (double)kli) - kp.g0mu[1];
+        // the error scale of the part kept in binary32
+        if (kp.cond_out)
+            kp.cond_out[p] = kp.K_D * ((double)sqrtf(fmaxf(r2, 0.0f)) + (double)fmaxf(r1, 0.0f));
+        const unsigned long long k = atomicAdd(kp.node_list_count, 1ULL);
+        kp.node_list[k] = NodeEntry{p, mask, gr.gsz};
+    }
+    __syncwarp();
+}
+
 // Evaluates point p of the request described by kp under `mode`; the whole
-// warp calls it with the same p.
-template <typename T, int NP, int NT, int CL>
+// warp calls it with the same p. Under MODE_NODES only the node groups in
+// gmask (gsz iterations each) are evaluated and added to G. GM: the group
+// handling of run_pass, fixed per call site (1 for MODE_NODES, 2 for the
+// binary32 bulk with partial routing, else 0).
+template <typename T, int NP, int NT, int CL, int GM = 0>
 __device__ __forceinline__ void eval_point(const KParams &kp, const AngTab<T, tab_size<NP>()> &tab,
                                            const T *stab, const void *srules, int64_t p, int mode,
-                                           int lane)
+                                           int lane, unsigned gmask = 0u, int gsz = 1)
 {
     double xr, xi;
     point_x(kp, p, xr, xi);
@@ -1214,7 +1481,7 @@ __device__ __forceinline__ void eval_point(const KParams &kp, const AngTab<T, ta
     if (xi == 0.0 && (xr < 0.0 || xr == kp.mu2)) {
         // the cut side of the real axis is undefined (NaN); G(mu2) = 0 by
         // the subtraction
-        if (mode != MODE_LIST64 && lane == 0) {
+        if ((mode == MODE_ALL || mode == MODE_BULK32) && lane == 0) {
             double v = xr < 0.0 ? __longlong_as_double(0x7ff8000000000000ULL) : 0.0;
             out[0] = v;
             out[1] = v;
@@ -1226,13 +1493,21 @@ __device__ __forceinline__ void eval_point(const KParams &kp, const AngTab<T, ta
         if (lane == 0) list_append(kp, p);
         return;
     }
+    Groups gr = {gmask, gsz, 0, nullptr, nullptr};
+    if constexpr (GM == 2) {
+        // partial routing: this warp's snapshot slot and group table (the
+        // caller checked the slot against kp.snap_slots)
+        const int64_t slot = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+        gr.snap = kp.snap + slot * (kMaxGroups * 32);
+        gr.gerr = group_err_slot();
+    }
     Acc<T> acc;
     acc.init();
     ErrAcc<T> ea = {T(0), T(0)};
     T qall = T(1e30);
     int pairs = 0, pfull = 0;
-    int nodes = point_sum<T, NP, NT, CL>(kp, tab, stab, srules, xr, xi, lane, acc, ea, qall, pairs,
-                                         pfull);
+    int nodes = point_sum<T, NP, NT, CL, GM>(kp, tab, stab, srules, xr, xi, lane, acc, ea, qall,
+                                             pairs, pfull, gr);
     if (kp.node_count && lane == 0)
         atomicAdd(kp.node_count, (unsigned long long)nodes * (unsigned long long)(2 * kp.npair));
     if (kp.pair_count) {
@@ -1247,21 +1522,19 @@ __device__ __forceinline__ void eval_point(const KParams &kp, const AngTab<T, ta
             if (kp.pair_full_count) atomicAdd(kp.pair_full_count, pf);
         }
     }
+    if constexpr (GM == 2) {
+        bulk_partial_epilogue(kp, p, lane, acc, (float)qall, gr, out);
+        return;
+    }
     double sr, si, cond;
     if constexpr (std::is_same<T, float>::value) {
         // binary32 throughout (the FP64 pipe is 1/64 of the binary32 one): the
         // lanes' compensated sums (hi, lo) are reduced as pairs, TwoSum on the
         // high parts; the error scale needs no more than binary32
         float hr = acc.sr, lr = acc.cr, hi = acc.si, li = acc.ci, s1 = ea.s1, s2 = ea.s2;
+        warp_pair_sum(hr, lr, hi, li);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
-            float ohr = __shfl_xor_sync(0xffffffffu, hr, o), olr = __shfl_xor_sync(0xffffffffu, lr, o);
-            float ohi = __shfl_xor_sync(0xffffffffu, hi, o), oli = __shfl_xor_sync(0xffffffffu, li, o);
-            float cr = 0.0f, ci = 0.0f;
-            two_sum_add(hr, cr, ohr);
-            two_sum_add(hi, ci, ohi);
-            lr = lr + olr + cr;
-            li = li + oli + ci;
             s1 += __shfl_xor_sync(0xffffffffu, s1, o);
             s2 += __shfl_xor_sync(0xffffffffu, s2, o);
         }
@@ -1273,13 +1546,21 @@ __device__ __forceinline__ void eval_point(const KParams &kp, const AngTab<T, ta
         si = warp_sum((double)acc.si + (double)acc.ci);
         cond = kp.K_D * (sqrt(warp_sum((double)ea.s2)) + warp_sum((double)ea.s1));
     }
+    if (mode == MODE_NODES) {
+        // the removed groups' part, added to what the bulk wrote
+        if (lane == 0) {
+            out[0] += kp.K_D * sr;
+            out[1] += kp.K_D * si;
+        }
+        return;
+    }
     float qpt = (float)qall;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) qpt = fminf(qpt, __shfl_xor_sync(0xffffffffu, qpt, o));
     if (lane == 0) {
-        double gr = kp.K_D * sr - kp.g0mu[0], gi = kp.K_D * si - kp.g0mu[1];
-        out[0] = gr;
-        out[1] = gi;
+        double gr0 = kp.K_D * sr - kp.g0mu[0], gi0 = kp.K_D * si - kp.g0mu[1];
+        out[0] = gr0;
+        out[1] = gi0;
         if (kp.cond_out) kp.cond_out[p] = cond;
         if (mode == MODE_BULK32 && kp.mixed_rtol > 0.0) {
             // rounding error of the binary32 sum: a small multiple of 2^-24
@@ -1288,7 +1569,7 @@ __device__ __forceinline__ void eval_point(const KParams &kp, const AngTab<T, ta
             // binary32 rounding of x and of the nodes that no such bound
             // holds; those points go to binary64 too.
             double est = kMixedErrFactor * 5.9604644775390625e-8 * cond;
-            if (!(est <= kp.mixed_rtol * sqrt(gr * gr + gi * gi)) || qpt < kMixedPinchQ)
+            if (!(est <= kp.mixed_rtol * sqrt(gr0 * gr0 + gi0 * gi0)) || qpt < kMixedPinchQ)
                 list_append(kp, p);
         }
     }
@@ -1336,25 +1617,63 @@ __device__ __forceinline__ void stage_tables(const KParams &kp, const T *gtab, i
 }
 
 // One request: warps take points from an atomic counter until none is left.
-template <typename T, int NP, int NT, int CL>
-__global__ void __launch_bounds__(256)
-eval_kernel(const __grid_constant__ KParams kp,
-            const __grid_constant__ AngTab<T, tab_size<NP>()> tab, const T *__restrict__ gtab)
+// GMK selects the launch's kind at compile time, so that each instantiation
+// carries only its own registers: 0 every point of MODE_ALL, MODE_LIST64 or
+// the binary32 bulk without partial routing; 1 MODE_NODES (the node groups of
+// the partially routed points); 2 the binary32 bulk with partial routing.
+template <typename T, int NP, int NT, int CL, int GMK>
+__device__ __forceinline__ void eval_loop(const KParams &kp, const AngTab<T, tab_size<NP>()> &tab,
+                                          const T *gtab)
 {
     const T *stab;
     const void *srules;
     stage_tables<T, NP>(kp, gtab, kp.npair, stab, srules);
     const int lane = threadIdx.x & 31;
-    const unsigned long long n =
-        kp.mode == MODE_LIST64 ? *kp.list_count : (unsigned long long)kp.npts;
+    // a warp without a snapshot slot evaluates its points in the plain bulk
+    // (the launcher sizes the slots for every warp the grid can hold)
+    const bool slot_ok =
+        (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5) < kp.snap_slots;
+    const unsigned long long n = kp.mode == MODE_LIST64  ? *kp.list_count
+                                 : kp.mode == MODE_NODES ? *kp.node_list_count
+                                                         : (unsigned long long)kp.npts;
     for (;;) {
         unsigned long long p = 0;
         if (lane == 0) p = atomicAdd(kp.counter, 1ULL);
         p = __shfl_sync(0xffffffffu, p, 0);
         if (p >= n) break;
-        int64_t pt = kp.mode == MODE_LIST64 ? kp.list[p] : (int64_t)p;
-        eval_point<T, NP, NT, CL>(kp, tab, stab, srules, pt, kp.mode, lane);
+        if constexpr (GMK == 1) {
+            const NodeEntry en = kp.node_list[p];
+            eval_point<T, NP, NT, CL, 1>(kp, tab, stab, srules, en.point, MODE_NODES, lane,
+                                         en.mask, en.gsz);
+        } else if constexpr (GMK == 2) {
+            if (slot_ok)
+                eval_point<T, NP, NT, CL, 2>(kp, tab, stab, srules, (int64_t)p, MODE_BULK32, lane);
+            else
+                eval_point<T, NP, NT, CL, 0>(kp, tab, stab, srules, (int64_t)p, MODE_BULK32, lane);
+        } else {
+            int64_t pt = kp.mode == MODE_LIST64 ? kp.list[p] : (int64_t)p;
+            eval_point<T, NP, NT, CL>(kp, tab, stab, srules, pt, kp.mode, lane);
+        }
     }
+}
+
+template <typename T, int NP, int NT, int CL, int GMK = 0>
+__global__ void __launch_bounds__(256)
+eval_kernel(const __grid_constant__ KParams kp,
+            const __grid_constant__ AngTab<T, tab_size<NP>()> tab, const T *__restrict__ gtab)
+{
+    eval_loop<T, NP, NT, CL, GMK>(kp, tab, gtab);
+}
+
+// the binary32 bulk with partial routing, held to the occupancy of the
+// plain bulk: 3 blocks of 256 threads per SM (2 for the variant kernels)
+template <typename T, int NP, int NT, int CL>
+__global__ void __launch_bounds__(256, CL ? 2 : 3)
+eval_bulk_partial_kernel(const __grid_constant__ KParams kp,
+                         const __grid_constant__ AngTab<T, tab_size<NP>()> tab,
+                         const T *__restrict__ gtab)
+{
+    eval_loop<T, NP, NT, CL, 2>(kp, tab, gtab);
 }
 
 // Many requests in one persistent launch (continuous batching): item i covers
@@ -1433,22 +1752,28 @@ inline const float *gtab_of<float>(const DevTables &tb) { return tb.ang32; }
 template <>
 inline const df *gtab_of<df>(const DevTables &tb) { return reinterpret_cast<const df *>(tb.ang_df); }
 
-template <typename T, int NP, int NT, int CL>
+template <typename T, int NP, int NT, int CL, int GMK = 0>
 static cudaError_t run_eval(const KParams &kp, const DevTables &tb, cudaStream_t st)
 {
     AngTab<T, tab_size<NP>()> tab;
     fill_tab(tab, tb, NP > 0 ? kp.npair : 0);
     size_t smem = smem_bytes<T, NP>(kp.npair, kp.rules_total);
+    const void *fn;
+    if constexpr (GMK == 2) fn = (const void *)eval_bulk_partial_kernel<T, NP, NT, CL>;
+    else fn = (const void *)eval_kernel<T, NP, NT, CL, GMK>;
     int blocks_per_sm = 0;
-    cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        &blocks_per_sm, (const void *)eval_kernel<T, NP, NT, CL>, 256, smem);
+    cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, fn, 256, smem);
     if (err != cudaSuccess) return err;
     if (blocks_per_sm < 1) blocks_per_sm = 1;
     int64_t blocks = (kp.npts + 7) / 8;
     int64_t cap = (int64_t)sm_count() * blocks_per_sm;
     if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
-    eval_kernel<T, NP, NT, CL><<<(unsigned)blocks, 256, smem, st>>>(kp, tab, gtab_of<T>(tb));
+    if constexpr (GMK == 2)
+        eval_bulk_partial_kernel<T, NP, NT, CL><<<(unsigned)blocks, 256, smem, st>>>(kp, tab,
+                                                                                    gtab_of<T>(tb));
+    else
+        eval_kernel<T, NP, NT, CL, GMK><<<(unsigned)blocks, 256, smem, st>>>(kp, tab, gtab_of<T>(tb));
     return cudaGetLastError();
 }
 

@@ -37,7 +37,8 @@ constexpr int kNaMaxG0Warps = 128;
 // layout of the scratch array (bytes, each block 256-byte aligned)
 constexpr size_t align256(size_t n) { return (n + 255) / 256 * 256; }
 constexpr size_t kOffRad = 0;
-constexpr size_t kOffSeg = kOffRad + align256(sizeof(double2) * kNaMaxRadial);
+constexpr size_t kOffRayp = kOffRad + align256(sizeof(double2) * kNaMaxRadial);
+constexpr size_t kOffSeg = kOffRayp + align256(sizeof(double2) * kNaMaxRadial);
 constexpr size_t kOffArc = kOffSeg + align256(sizeof(double2) * (kNaMaxRadial / 4));
 constexpr size_t kOffAng = kOffArc + align256(sizeof(double2) * (kNaMaxRadial / 4));
 constexpr size_t kOffPart = kOffAng + align256(sizeof(double) * 3 * (kNaMaxAngular / 2));
@@ -48,7 +49,7 @@ constexpr size_t kNoAllocBytes = kOffTicket + align256(sizeof(unsigned));
 
 }  // namespace
 
-// The scratch of gfc_eval_points_noalloc (about 150 KB).
+// The scratch of gfc_eval_points_noalloc (about 170 KB).
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
 namespace {
@@ -58,7 +59,7 @@ unsigned char *g_na_ptr[64];     // device address of the array, per device
 bool g_na_ready[64];
 
 // host staging of the tables (static: nothing allocated per call)
-double2 h_rad[kNaMaxRadial], h_seg[kNaMaxRadial / 4], h_arc[kNaMaxRadial / 4];
+double2 h_rad[kNaMaxRadial], h_rayp[kNaMaxRadial], h_seg[kNaMaxRadial / 4], h_arc[kNaMaxRadial / 4];
 double h_ang[3 * (kNaMaxAngular / 2)];
 double h_t[kNaMaxAngular / 2], h_e[kNaMaxAngular / 2], h_g[kNaMaxAngular / 2];
 double h_gx[kNaMaxRadial], h_gw[kNaMaxRadial];
@@ -148,6 +149,9 @@ extern "C" int gfc_eval_points_noalloc(const gfc_propagator *prop, const gfc_par
     for (int k = 0; k < nr; ++k) {
         double t = 0.5 * (h_gx[k] + 1.0), omt = 0.5 * (1.0 - h_gx[k]);
         h_rad[k] = make_double2(L * t / omt, L / (omt * omt) * 0.5 * h_gw[k]);
+        // (rho^2, rho^(D-1) W) of the binary64 ray nodes
+        const double r2 = h_rad[k].x * h_rad[k].x;
+        h_rayp[k] = make_double2(r2, (params->dim == 4 ? r2 * h_rad[k].x : r2) * h_rad[k].y);
     }
     gl_into(ns, h_gx, h_gw);
     for (int k = 0; k < ns; ++k) {
@@ -179,6 +183,7 @@ extern "C" int gfc_eval_points_noalloc(const gfc_propagator *prop, const gfc_par
     // copies from pageable host memory return once the source has been read,
     // so the static staging arrays can be refilled by the next call
     if ((e = cudaMemcpyAsync(base + kOffRad, h_rad, sizeof(double2) * nr, cudaMemcpyHostToDevice, st)) ||
+        (e = cudaMemcpyAsync(base + kOffRayp, h_rayp, sizeof(double2) * nr, cudaMemcpyHostToDevice, st)) ||
         (e = cudaMemcpyAsync(base + kOffSeg, h_seg, sizeof(double2) * ns, cudaMemcpyHostToDevice, st)) ||
         (e = cudaMemcpyAsync(base + kOffArc, h_arc, sizeof(double2) * ns, cudaMemcpyHostToDevice, st)) ||
         (e = cudaMemcpyAsync(base + kOffAng, h_ang, sizeof(double) * 3 * np, cudaMemcpyHostToDevice, st)))
@@ -194,6 +199,7 @@ extern "C" int gfc_eval_points_noalloc(const gfc_propagator *prop, const gfc_par
     kp.n_s = ns;
     kp.npair = np;
     kp.rad64 = reinterpret_cast<const double2 *>(base + kOffRad);
+    kp.rayp64 = reinterpret_cast<const double2 *>(base + kOffRayp);
     kp.seg64 = reinterpret_cast<const double2 *>(base + kOffSeg);
     kp.arc64 = reinterpret_cast<const double2 *>(base + kOffArc);
     kp.L = L;

@@ -21,7 +21,10 @@ constexpr int kThreads = 256;
 // OP: 0 binary64 FMA, 1 binary64 multiply, 2 binary64 add, 3 binary32 FMA,
 // 4 binary32 approximate reciprocal (each followed by a binary32 add of a
 // tiny constant, which the FMA pipes absorb), 5 binary64 FMA interleaved
-// with an independent binary32 FMA chain; ILP independent chains per thread.
+// with an independent binary32 FMA chain, 6 binary64 FMA, multiply and add in
+// the proportions 5 : 2 : 1 (those of the binary64 evaluation kernel, whose
+// FP64 pipe issues mixed streams faster than any one operation alone); ILP
+// independent chains per thread.
 // Thread 0 of block 0 records the SM clock and the global timer around its
 // loop, so that the SM frequency of the launch is known.
 template <int OP, int ILP>
@@ -33,7 +36,7 @@ __global__ void __launch_bounds__(kThreads) probe_kernel(int iters, double b, do
         c0 = clock64();
         asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
     }
-    if constexpr (OP <= 2 || OP == 5) {
+    if constexpr (OP <= 2 || OP >= 5) {
         double a[ILP];
         float f[OP == 5 ? ILP : 1];
         const float bf = (float)b, cf = (float)c;
@@ -46,9 +49,18 @@ __global__ void __launch_bounds__(kThreads) probe_kernel(int iters, double b, do
             for (int u = 0; u < kUnroll; ++u)
 #pragma unroll
                 for (int j = 0; j < ILP; ++j) {
-                    if constexpr (OP == 0 || OP == 5) a[j] = fma(a[j], b, c);
-                    else if constexpr (OP == 1) a[j] = a[j] * b;
-                    else a[j] = a[j] + c;
+                    if constexpr (OP == 0 || OP == 5) {
+                        a[j] = fma(a[j], b, c);
+                    } else if constexpr (OP == 1) {
+                        a[j] = a[j] * b;
+                    } else if constexpr (OP == 2) {
+                        a[j] = a[j] + c;
+                    } else {
+                        const int q = (j + u) & 7;   // the op of chain j at step u
+                        if (q < 5) a[j] = fma(a[j], b, c);
+                        else if (q < 7) a[j] = a[j] * b;
+                        else a[j] = a[j] + c;
+                    }
                     if constexpr (OP == 5) f[j] = fmaf(f[j], bf, cf);
                 }
         }
@@ -113,7 +125,8 @@ double time_probe(int op, int ilp, int blocks, int iters, double *sink, cudaStre
     case 2: e = launch_probe<2>(ilp, blocks, iters, sink, st); break;
     case 3: e = launch_probe<3>(ilp, blocks, iters, sink, st); break;
     case 4: e = launch_probe<4>(ilp, blocks, iters, sink, st); break;
-    default: e = launch_probe<5>(ilp, blocks, iters, sink, st); break;
+    case 5: e = launch_probe<5>(ilp, blocks, iters, sink, st); break;
+    default: e = launch_probe<6>(ilp, blocks, iters, sink, st); break;
     }
     if (e != cudaSuccess) return -1.0;
     if (cudaEventRecord(e1, st) != cudaSuccess) return -1.0;
@@ -148,9 +161,9 @@ extern "C" int gfc_measure_pipe_peaks(gfc_pipe_peaks *out, double seconds, void 
     }
     // every probe at 8 and 16 chains per thread and 4 and 8 blocks per SM;
     // the best configuration gives the pipe's rate
-    double rate[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0}, mhz[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    double rate[7] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0}, mhz[7] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
     int rc = GFC_OK;
-    for (int op = 0; op < 6 && rc == GFC_OK; ++op) {
+    for (int op = 0; op < 7 && rc == GFC_OK; ++op) {
         for (int cfg = 0; cfg < 4 && rc == GFC_OK; ++cfg) {
             const int ilp = cfg & 1 ? 16 : 8, blocks = sms * (cfg & 2 ? 8 : 4);
             const double per = seconds / 4.0;
@@ -196,6 +209,7 @@ extern "C" int gfc_measure_pipe_peaks(gfc_pipe_peaks *out, double seconds, void 
         mhz[0] = mhz[5];
     }
     out->dfma_per_s = rate[0];
+    out->fp64_mix_per_s = rate[6];
     out->dfma_mhz = mhz[0];
     out->ffma_mhz = mhz[3];
     out->dmul_per_s = rate[1];

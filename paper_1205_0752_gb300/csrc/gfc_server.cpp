@@ -1,16 +1,20 @@
 // Serving runtime of libgfc: continuous batching of grid requests.
 //
 // A scheduler thread admits queued requests into device slots while the
-// server's memory budget and slot count allow (FIFO), computes each admitted
+// server's memory budget and slot count allow, computes each admitted
 // request's G0(mu2) on the device, then carves the requests' points into work
 // items and issues persistent batched launches (eval_batch_kernel). One launch
-// mixes items of every active request that shares its kernel variant
+// mixes items of the active requests that share its kernel variant
 // (binary32/binary64, angular order, dimension, number of terms, launch
 // mode); variants run on separate streams, so requests of different kinds
-// overlap on the device. Each launch is sized to a bounded amount of work, so
-// a request that arrives while others run joins the next launches. When all
-// items of a request have finished, its grid is copied to the host through a
-// pinned staging buffer, its slot and memory are freed, and its latency
+// overlap on the device. Admission and launch composition are cost-aware:
+// requests are served least estimated remaining work first, aged by their
+// waiting time so that none starves. Each launch is sized to a bounded amount
+// of work and only a few are on the device at once, so a request that
+// arrives while others run joins the next launches, on a high-priority stream
+// when it is short. When all items of a request have finished, its grid is
+// copied to the host through a pinned staging buffer (or was written in
+// place, for device outputs), its slot and memory are freed, and its latency
 // (submit to completion) is recorded.
 #include <cuda_runtime.h>
 
@@ -41,12 +45,20 @@ namespace {
 
 using clk = std::chrono::steady_clock;
 
-constexpr int kStreams = 4;          // launch streams
-constexpr int kRing = 16;            // launches in flight at most
+constexpr int kStreams = 4;          // launch streams: 0, 1 high priority; 2, 3 low
+constexpr int kRing = 16;            // launch records
+constexpr int kMaxInflight = 6;      // launches queued or running on the device at once
 constexpr int kMaxItems = 4096;      // work items per launch
 constexpr int kG0Warps = 512;
-// work per launch in units of binary32 pair evaluations (about 20-40 ms)
-constexpr double kLaunchWork = 1.5e11;
+// work per launch in units of binary32 pair evaluations (about 10-20 ms)
+constexpr double kLaunchWork = 7.5e10;
+// ageing of the scheduling key: work units the device completes per second,
+// so that a request that has waited t seconds ranks as if it had the work
+// the device does in t seconds less left
+constexpr double kAgeRate = kLaunchWork / 0.015;
+// fraction of a mixed request's points that its fallback is expected to
+// re-evaluate (the key's estimate until the count is known)
+constexpr double kMixedRouted = 0.45;
 constexpr double kFp64Weight = 24.0; // binary64 pair cost in binary32 pair units
 constexpr double kDfWeight = 6.0;    // double-float pair cost in binary32 pair units
 
@@ -85,7 +97,7 @@ struct Request {
     void *pinned = nullptr;
     size_t pinned_size = 0;
     cudaEvent_t copy_done = nullptr;
-    double cost_per_point = 1.0;
+    double work_left = 0.0;             // estimated work not yet launched (units of kLaunchWork)
     clk::time_point t_submit, t_admit, t_done;
     bool admitted = false;
     int64_t launches = 0;               // batched launches that carried its work
@@ -188,6 +200,25 @@ double work_per_point(const Request &r, int arith)
     // the closed-form angular integral costs about as much as four pairs
     double w = nodes * std::max(npair_of(&r.params), 4) * terms;
     return arith == ARITH_F32 ? w : (arith == ARITH_DF ? w * kDfWeight : w * kFp64Weight);
+}
+
+// Estimated work of a whole request (binary32-pair units): every point in its
+// arithmetic; for mixed precision the binary32 bulk and the expected fallback.
+double request_work(const Request &r)
+{
+    if (r.params.precision != GFC_MIXED) {
+        const int ar = r.params.precision == GFC_F32X2 ? ARITH_DF : ARITH_F64;
+        return r.npts * work_per_point(r, ar);
+    }
+    const int fb = r.params.mixed_fallback == GFC_F32X2 ? ARITH_DF : ARITH_F64;
+    return r.npts * (work_per_point(r, ARITH_F32) + kMixedRouted * work_per_point(r, fb));
+}
+
+// Scheduling key: the least first (shortest remaining work, aged by waiting).
+double sched_key(const Request &r, clk::time_point now)
+{
+    const double wait = std::chrono::duration<double>(now - r.t_submit).count();
+    return r.work_left - kAgeRate * wait;
 }
 
 void release_request(gfc_server *s, Request *r)
@@ -317,9 +348,16 @@ bool request_complete(const Request *r)
     return true;
 }
 
-// One batched launch per variant with pending points, while ring entries are free.
+// Batched launches, one per kernel variant with pending points, the variant
+// whose most urgent request (least sched_key) ranks first going first, while
+// fewer than kMaxInflight launches are on the device. Within a launch the
+// variant's requests are served least key first (shortest remaining work,
+// aged), each up to the launch's work budget; a launch whose first request
+// is urgent (key below two launches of work) goes to a high-priority stream,
+// so that its blocks start ahead of those of launches for longer requests.
 void issue_launches(gfc_server *s)
 {
+    const clk::time_point now = clk::now();
     std::map<GroupKey, std::vector<std::pair<Request *, int>>> groups;
     for (Request *r : s->active) {
         if (r->canceled || r->failed) continue;
@@ -332,7 +370,22 @@ void issue_launches(gfc_server *s)
             groups[k].push_back({r, p});
         }
     }
+    // the groups in the order of their most urgent request, each group's
+    // requests least key first
+    std::vector<std::pair<double, GroupKey>> order;
     for (auto &kv : groups) {
+        auto &members = kv.second;
+        std::stable_sort(members.begin(), members.end(), [now](const auto &a, const auto &b) {
+            return sched_key(*a.first, now) < sched_key(*b.first, now);
+        });
+        order.push_back({sched_key(*members.front().first, now), kv.first});
+    }
+    std::stable_sort(order.begin(), order.end(),
+                     [](const auto &a, const auto &b) { return a.first < b.first; });
+    int inflight = 0;
+    for (int i = 0; i < kRing; ++i) inflight += s->ring[i].busy ? 1 : 0;
+    for (auto &og : order) {
+        if (inflight >= kMaxInflight) return;
         int li = -1;
         for (int i = 0; i < kRing; ++i)
             if (!s->ring[i].busy) {
@@ -341,46 +394,45 @@ void issue_launches(gfc_server *s)
             }
         if (li < 0) return;
         LaunchRec &L = s->ring[li];
-        const GroupKey &key = kv.first;
+        const GroupKey &key = og.second;
         const int arith = std::get<0>(key);
         const int mode = std::get<4>(key);
-        auto &members = kv.second;
-        // round-robin over the group's requests, each item bounded so that no
-        // request takes the whole launch when others wait
+        auto &members = groups[key];
+        const bool urgent = og.first < 2.0 * kLaunchWork;
+        // least key first, each request up to what the budget has left
         double budget = kLaunchWork;
         int nitems = 0;
         int64_t total = 0;
         L.reqs.clear();
         std::map<std::pair<Request *, int>, int64_t> count;
-        bool progress = true;
-        while (budget > 0 && nitems < kMaxItems && progress) {
-            progress = false;
-            for (auto &m : members) {
-                Request *r = m.first;
-                Phase &ph = r->phases[m.second];
-                if (ph.next >= ph.end || nitems >= kMaxItems || budget <= 0) continue;
-                double wpp = work_per_point(*r, arith);
-                double share = std::max(budget / members.size(), wpp * 256.0);
-                int64_t n = (int64_t)std::max(1.0, share / wpp);
-                n = std::min(n, ph.end - ph.next);
-                L.items_host[nitems] = BatchItem{r->slot, 0, ph.next, ph.next + n};
-                L.offs_host[nitems] = total;
-                total += n;
-                ph.next += n;
-                budget -= n * wpp;
-                count[{r, m.second}] += 1;
-                ++nitems;
-                progress = true;
-            }
+        for (auto &m : members) {
+            if (budget <= 0 || nitems >= kMaxItems) break;
+            Request *r = m.first;
+            Phase &ph = r->phases[m.second];
+            const double wpp = work_per_point(*r, arith);
+            // items of at least 256 points (or what is left), at most the budget
+            int64_t n = (int64_t)std::max(256.0, budget / wpp);
+            n = std::min(n, ph.end - ph.next);
+            if (n <= 0) continue;
+            L.items_host[nitems] = BatchItem{r->slot, 0, ph.next, ph.next + n};
+            L.offs_host[nitems] = total;
+            total += n;
+            ph.next += n;
+            budget -= n * wpp;
+            r->work_left = std::max(0.0, r->work_left - n * wpp);
+            count[{r, m.second}] += 1;
+            ++nitems;
         }
         if (nitems == 0) continue;
+        ++inflight;
         for (auto &c : count) {
             c.first.first->phases[c.first.second].items_out += c.second;
             c.first.first->launches++;
             L.reqs.push_back(std::make_tuple(c.first.first, c.first.second, c.second));
         }
-        cudaStream_t st = s->streams[s->next_stream];
-        s->next_stream = (s->next_stream + 1) % kStreams;
+        // high-priority streams 0 and 1, low-priority 2 and 3, alternating
+        const int si = (urgent ? 0 : 2) + (s->next_stream++ & 1);
+        cudaStream_t st = s->streams[si];
         L.failed = false;
         L.fail_msg.clear();
         auto chk = [&L](cudaError_t e, const char *what) {
@@ -455,6 +507,7 @@ bool progress(gfc_server *s)
                 if (q == cudaSuccess) {
                     p1.end = (int64_t)s->slot_counts_host[r->slot];
                     r->routed = p1.end;
+                    r->work_left = p1.end * work_per_point(*r, p1.arith);
                     r->count_pending = false;
                     changed = true;
                 } else if (q != cudaErrorNotReady) {
@@ -535,16 +588,23 @@ void scheduler(gfc_server *s)
     cudaSetDevice(s->device);
     std::unique_lock<std::mutex> lk(s->mu);
     for (;;) {
-        // admission, FIFO
+        // admission: the queued request with the least key (shortest work,
+        // aged by waiting) that fits the budget, while slots are free
         while (!s->queue.empty() && !s->free_slots.empty()) {
-            Request *r = s->queue.front();
-            if (r->canceled) {
-                s->queue.pop_front();
-                finish(s, r, GFC_ECANCELED);
-                continue;
+            const clk::time_point now = clk::now();
+            auto best = s->queue.end();
+            double bk = 0.0;
+            for (auto it = s->queue.begin(); it != s->queue.end(); ++it) {
+                if ((*it)->canceled || s->bytes_in_use + (*it)->bytes > s->budget) continue;
+                const double k = sched_key(**it, now);
+                if (best == s->queue.end() || k < bk) {
+                    best = it;
+                    bk = k;
+                }
             }
-            if (s->bytes_in_use + r->bytes > s->budget) break;
-            s->queue.pop_front();
+            if (best == s->queue.end()) break;
+            Request *r = *best;
+            s->queue.erase(best);
             s->bytes_in_use += r->bytes;
             int rc = admit(s, r);
             if (rc != GFC_OK) {
@@ -594,8 +654,12 @@ int gfc_server_create(int device, size_t hbm_budget_bytes, int max_slots, gfc_se
     bool ok = cudaStreamCreateWithFlags(&s->admit_stream, cudaStreamNonBlocking) == cudaSuccess &&
               cudaStreamCreateWithFlags(&s->copy_stream, cudaStreamNonBlocking) == cudaSuccess &&
               cudaEventCreateWithFlags(&s->admit_event, cudaEventDisableTiming) == cudaSuccess;
+    // launch streams: two at the device's greatest priority, two at its least
+    int prio_lo = 0, prio_hi = 0;
+    cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
     for (int i = 0; i < kStreams && ok; ++i)
-        ok = cudaStreamCreateWithFlags(&s->streams[i], cudaStreamNonBlocking) == cudaSuccess;
+        ok = cudaStreamCreateWithPriority(&s->streams[i], cudaStreamNonBlocking,
+                                          i < 2 ? prio_hi : prio_lo) == cudaSuccess;
     ok = ok && cudaMalloc((void **)&s->slots_dev, sizeof(KParams) * max_slots) == cudaSuccess &&
          cudaMallocHost((void **)&s->slots_host, sizeof(KParams) * max_slots) == cudaSuccess &&
          cudaMalloc((void **)&s->g0mu_dev, sizeof(double) * 2 * max_slots) == cudaSuccess &&
@@ -659,6 +723,7 @@ int gfc_server_submit(gfc_server *s, const gfc_propagator *prop, const gfc_param
     r->bytes = ((r->G_on_device ? 0 : 16) + (params->precision == GFC_MIXED ? 8 : 0)) *
                (size_t)r->npts;
     r->t_submit = clk::now();
+    r->work_left = request_work(*r);
     std::lock_guard<std::mutex> lk(s->mu);
     if (s->stopping) return fail(GFC_EBUSY, "server is shutting down");
     if (r->bytes > s->budget) {
