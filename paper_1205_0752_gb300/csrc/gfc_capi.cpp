@@ -797,8 +797,8 @@ static void fill_kparams_tables(KParams &kp, const gfc_params *p, const Tables &
     for (int r = 0; r < T.nrule; ++r) {
         kp.rule_off[r] = T.rule_off[r];
         kp.rule_n[r] = T.rule_n[r];
-        kp.rho_min32[r] = T.rho_min32[r];
-        kp.rho_min64[r] = T.rho_min64[r];
+        kp.sig_min32[r] = (float)(0.5 * ((double)T.rho_min32[r] + 1.0 / (double)T.rho_min32[r]));
+        kp.sig_min64[r] = (float)(0.5 * ((double)T.rho_min64[r] + 1.0 / (double)T.rho_min64[r]));
     }
     kp.rules64 = T.rules64;
     kp.rules32 = T.rules32;
@@ -812,6 +812,9 @@ static void fill_kparams_tables(KParams &kp, const gfc_params *p, const Tables &
             kp.dfc[2 * i] = v.hi;
             kp.dfc[2 * i + 1] = v.lo;
         }
+        const df om(kp.Omega);
+        kp.om_df[0] = om.hi;
+        kp.om_df[1] = om.lo;
     }
     kp.cut_band = p->cut_band;
     kp.pinch_angle = p->pinch_angle;

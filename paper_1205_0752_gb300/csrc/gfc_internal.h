@@ -73,6 +73,7 @@ struct KParams {
     // and as double-float (hi, lo) pairs, for the kernels of those arithmetics
     float f32c[6];
     float dfc[12];
+    float om_df[2];      // Omega as a double-float (hi, lo) pair
     int use_grid;        // 1: x from the grid spec, 0: from x[]
     int64_t npts;
     // grid (Kernel 1)
@@ -114,7 +115,8 @@ struct KParams {
     // pair sum of 1/(1 - w t) to rounding level when rho(w) >= rho_min{32,64}[r]
     int nrule;
     int rule_off[kMaxRules], rule_n[kMaxRules];
-    float rho_min32[kMaxRules], rho_min64[kMaxRules];
+    // (the thresholds as sigma = (rho + 1/rho)/2, which the kernels compare)
+    float sig_min32[kMaxRules], sig_min64[kMaxRules];
     const double *rules64;   // per node (tau, gamma, gamma tau)
     const float4 *rules32;   // per node (tau, gamma, gamma tau, 0)
     const float2 *rules_df;  // per node (tau, gamma, gamma tau) as double-float

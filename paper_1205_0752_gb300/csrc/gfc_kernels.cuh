@@ -48,6 +48,12 @@ constexpr float kMixedPinchQ = 1e-5f;   // |1 - w t|^2 below which a point is ro
 #define GFC_PARTIAL_MARGIN 4.0
 #endif
 constexpr double kPartialMargin = GFC_PARTIAL_MARGIN;
+// partial routing applies to points whose estimate fails by at most this
+// factor; beyond it every group is evaluated again
+#ifndef GFC_PARTIAL_MAX
+#define GFC_PARTIAL_MAX 32.0
+#endif
+constexpr double kPartialMax = GFC_PARTIAL_MAX;
 // weight of the pole terms of kappa on binary32 ray nodes with y exact
 #ifndef GFC_POLE_WEIGHT
 #define GFC_POLE_WEIGHT 0.5
@@ -650,27 +656,50 @@ __device__ __forceinline__ T q_horner(T t, T w2, T m2wr)
     return fma(fma(w2, t, m2wr), t, T(1));
 }
 
-// Bernstein-ellipse parameter of the pole t = 1/w of 1/(1 - w t) for the
-// interval [0, 1]: rho = |s0 + sqrt(s0 - 1) sqrt(s0 + 1)| >= 1, s0 = 2/w - 1.
-__device__ __forceinline__ float rho_of(float wr, float wi)
+// Where the pole t = 1/w of 1/(1 - w t) lies relative to the interval [0, 1]:
+// on the Bernstein ellipse of parameter rho >= 1, i.e. the ellipse with foci
+// t = 0 and t = 1 through 1/w, whose distances to the foci sum to
+// (rho + 1/rho)/2 in units of the interval. That sum is
+//   sigma = (|1/w| + |1/w - 1|) = (1 + |1 - w|) / |w|,
+// monotone in rho, so the rule thresholds are compared in sigma. Two
+// reciprocal square roots (the hardware approximations: the thresholds carry
+// a factor 10 of margin in the error they bound); w = 0 gives infinity (the
+// smallest rule), a pole on the interval (w = 1/t) 1/|w| <= 1 (the full table).
+__device__ __forceinline__ float sigma_of(float wr, float wi)
 {
-    float n2 = wr * wr + wi * wi;
+    const float n2 = wr * wr + wi * wi;
     if (!(n2 > 0.0f)) return __int_as_float(0x7f800000);
-    C<float> s0 = {2.0f * wr / n2 - 1.0f, -2.0f * wi / n2};
-    C<float> a = csqrt_p(C<float>{s0.r - 1.0f, s0.i}), b = csqrt_p(C<float>{s0.r + 1.0f, s0.i});
-    C<float> z = s0 + a * b;
-    float m = sqrtf(cabs2(z));
-    return m >= 1.0f ? m : 1.0f / m;
+    const float dr = 1.0f - wr;
+    const float q = fmaxf(fmaf(dr, dr, wi * wi), 1e-30f);
+    return fmaf(q, rsqrtf(q), 1.0f) * rsqrtf(n2);
+}
+
+// An approximate binary32 value for the rule selection: binary32 as is, the
+// high part of a double-float, and binary64 truncated by integer operations
+// on its bits (relative error below 2^-23; a conversion instruction would
+// occupy the FP64 pipe, which bounds the binary64 kernel). Magnitudes below
+// binary32's normal range give 0, above it infinity.
+__device__ __forceinline__ float to_f32(float v) { return v; }
+__device__ __forceinline__ float to_f32(df v) { return v.hi; }
+__device__ __forceinline__ float to_f32(double v)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
+    const int e = (int)((hi >> 20) & 0x7ffu) - 1023 + 127;
+    const unsigned sign = hi & 0x80000000u;
+    if (e <= 0) return __int_as_float((int)sign);
+    if (e >= 255) return __int_as_float((int)(sign | 0x7f800000u));
+    return __int_as_float((int)(sign | ((unsigned)e << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29)));
 }
 
 template <typename T>
-__device__ __forceinline__ float rho_min(const KParams &kp, int r);
+__device__ __forceinline__ float sig_min(const KParams &kp, int r);
 template <>
-__device__ __forceinline__ float rho_min<float>(const KParams &kp, int r) { return kp.rho_min32[r]; }
+__device__ __forceinline__ float sig_min<float>(const KParams &kp, int r) { return kp.sig_min32[r]; }
 template <>
-__device__ __forceinline__ float rho_min<double>(const KParams &kp, int r) { return kp.rho_min64[r]; }
+__device__ __forceinline__ float sig_min<double>(const KParams &kp, int r) { return kp.sig_min64[r]; }
 template <>
-__device__ __forceinline__ float rho_min<df>(const KParams &kp, int r) { return kp.rho_min64[r]; }
+__device__ __forceinline__ float sig_min<df>(const KParams &kp, int r) { return kp.sig_min64[r]; }
 
 // one node (tau, gamma, gamma tau) of a compressed rule in shared memory
 __device__ __forceinline__ void rule_node(const void *srules, int k, double &t, double &e,
@@ -733,11 +762,11 @@ __device__ __forceinline__ int pair_sums(const KParams &kp, const AngTab<T, tab_
     // term, made uniform over the lanes that run together
     int rule = kp.nrule;
     {
-        float rho = __int_as_float(0x7f800000);
+        float sig = __int_as_float(0x7f800000);
 #pragma unroll
-        for (int s = 0; s < NT; ++s) rho = fminf(rho, rho_of((float)w[s].r, (float)w[s].i));
+        for (int s = 0; s < NT; ++s) sig = fminf(sig, sigma_of(to_f32(w[s].r), to_f32(w[s].i)));
         for (int q = 0; q < kp.nrule; ++q)
-            if (rho >= rho_min<T>(kp, q)) {
+            if (sig >= sig_min<T>(kp, q)) {
                 rule = q;
                 break;
             }
@@ -901,15 +930,17 @@ struct PassPre {
     C<T> xm[NT], xml[NT];   // x + M2_t rounded (binary32: and its remainder, TwoSum)
     C<T> x4;                // 4 x
     C<T> omxl[NT];          // binary32: Omega (x + M2_t) - omx (the product in binary64)
+    C<T> xlo;               // binary32 with partial routing: x less its binary32 value
 };
 
 
 
 template <typename T, int NT, int ACC = 0>
 __device__ __forceinline__ PassPre<T, NT> pass_pre(const KParams &kp, const Plan<T> &P, int pass,
-                                                   C<T> x)
+                                                   C<T> x, C<T> xlo = {T(0), T(0)})
 {
     PassPre<T, NT> pp;
+    pp.xlo = xlo;
     pp.nt = P.nterm[pass];
     pp.x4 = T(4) * x;
     const T Om = T(kp.Omega);
@@ -922,14 +953,6 @@ __device__ __forceinline__ PassPre<T, NT> pass_pre(const KParams &kp, const Plan
         if constexpr (!(std::is_same<T, float>::value && ACC)) pp.omx[s] = Om * (x + tm.m2q);
         pp.full[s] = tm.full;
         pp.same[s] = !tm.full && tm.m2k.r == tm.m2q.r && tm.m2k.i == tm.m2q.i;
-        if constexpr (std::is_same<T, float>::value && ACC) {
-            // Omega (x + M2) to double-float accuracy: rounded once per pass it
-            // would shift every node's leading term alike (see node_value)
-            const double orr = kp.Omega * ((double)x.r + (double)tm.m2q.r);
-            const double oii = kp.Omega * ((double)x.i + (double)tm.m2q.i);
-            pp.omx[s] = {(float)orr, (float)oii};
-            pp.omxl[s] = {(float)(orr - (double)pp.omx[s].r), (float)(oii - (double)pp.omx[s].i)};
-        }
         if constexpr (std::is_same<T, float>::value) {
             // TwoSum (Knuth): x + M2 = xm + xml exactly
             const C<T> m = tm.m2q;
@@ -937,6 +960,24 @@ __device__ __forceinline__ PassPre<T, NT> pass_pre(const KParams &kp, const Plan
             const T br = sr - x.r, bi = si - x.i;
             pp.xm[s] = {sr, si};
             pp.xml[s] = {(x.r - (sr - br)) + (m.r - br), (x.i - (si - bi)) + (m.i - bi)};
+        }
+        if constexpr (std::is_same<T, float>::value && ACC) {
+            // Omega (x + M2) to double-float accuracy, in binary32 operations
+            // (TwoProduct of the high parts, the low terms gathered): rounded
+            // once per pass it would shift every node's leading term alike
+            // (see node_value). The asm keeps the four values in registers:
+            // the compiler would otherwise recompute them per node.
+            // x + M2 = xm + xml with x's own remainder (x less its binary32
+            // value) in xml: every node's a = x + y + M2 then holds x to
+            // double-float accuracy
+            pp.xml[s] = pp.xml[s] + xlo;
+            const float oh = kp.om_df[0], ol = kp.om_df[1];
+            float pr = oh * pp.xm[s].r, pi = oh * pp.xm[s].i;
+            float er = fmaf(oh, pp.xm[s].r, -pr) + (oh * pp.xml[s].r + ol * pp.xm[s].r);
+            float ei = fmaf(oh, pp.xm[s].i, -pi) + (oh * pp.xml[s].i + ol * pp.xm[s].i);
+            asm volatile("" : "+f"(pr), "+f"(pi), "+f"(er), "+f"(ei));
+            pp.omx[s] = {pr, pi};
+            pp.omxl[s] = {er, ei};
         }
     }
     return pp;
@@ -1006,7 +1047,13 @@ __device__ __forceinline__ C<T> node_value(const KParams &kp, const AngTab<T, ta
         if constexpr (f32) {
             // binary32 keeps v = 4u itself (its registers are the scarcer)
             u[s] = T(4) * (nd.y * ia[s]);
-            w[s] = (x * u[s]) * ia[s];
+            if constexpr (ACC) {
+                // w = x v / a with x to double-float accuracy (x + its remainder)
+                const C<T> xv = x * u[s], lv = pp.xlo * u[s];
+                w[s] = C<T>{xv.r + lv.r, xv.i + lv.i} * ia[s];
+            } else {
+                w[s] = (x * u[s]) * ia[s];
+            }
         } else {
             u[s] = nd.y * ia[s];
             w[s] = (pp.x4 * u[s]) * ia[s];
@@ -1215,9 +1262,9 @@ __device__ __forceinline__ int run_pass(const KParams &kp, const AngTab<T, tab_s
                                         const T *stab, const void *srules, const Plan<T> &P,
                                         int pass, C<T> x, C<T> e2, C<T> eD, int lane, Acc<T> &acc,
                                         ErrAcc<T> &ea, T &qall, int &pairs, int &pfull,
-                                        const Groups &gr, GroupCursor &cur, C<T> e2lo)
+                                        const Groups &gr, GroupCursor &cur, C<T> e2lo, C<T> xlo)
 {
-    const PassPre<T, NTT> pp = pass_pre<T, NTT, (GM == 2 ? 1 : 0)>(kp, P, pass, x);
+    const PassPre<T, NTT> pp = pass_pre<T, NTT, (GM == 2 ? 1 : 0)>(kp, P, pass, x, xlo);
     const bool ray = P.kind[pass] == PASS_RAY;
     const int nn = ray ? kp.n_r : 3 * kp.n_s + kp.n_r;
     DetourPre<T> *dps = detour_slot<T>();
@@ -1294,7 +1341,7 @@ __device__ __forceinline__ int point_sum(const KParams &kp, const AngTab<T, tab_
     const C<T> x = cvt<T>(xr, xi);
     // e^{i D theta} of the ray, once per point
     C<T> e2 = P.eth * P.eth;
-    C<T> e2lo = {T(0), T(0)};
+    C<T> e2lo = {T(0), T(0)}, xlo = {T(0), T(0)};
     if constexpr (GM == 2) {
         // the binary32 bulk with partial routing puts its ray nodes on the
         // exact direction x/|x| (binary32 value and remainder): the node
@@ -1305,6 +1352,10 @@ __device__ __forceinline__ int point_sum(const KParams &kp, const AngTab<T, tab_
         const double dr = xr / ax, di = xi / ax;
         e2 = {(float)dr, (float)di};
         e2lo = {(float)(dr - (double)e2.r), (float)(di - (double)e2.i)};
+        // and x itself: its remainder joins every node's a = x + y + M2 and w
+        xlo = {(float)(xr - (double)x.r), (float)(xi - (double)x.i)};
+        // (held in registers: not recomputed in binary64 per node)
+        asm volatile("" : "+f"(e2.r), "+f"(e2.i), "+f"(e2lo.r), "+f"(e2lo.i), "+f"(xlo.r), "+f"(xlo.i));
     }
     const C<T> eD = kp.dim == 4 ? e2 * e2 : e2 * P.eth;
     if (GM == 2) {
@@ -1322,10 +1373,10 @@ __device__ __forceinline__ int point_sum(const KParams &kp, const AngTab<T, tab_
         if (NT > 1 && P.nterm[pass] == 2)
             total += run_pass<T, NP, (NT > 1 ? 2 : 1), CL, GM>(kp, tab, stab, srules, P, pass, x, e2,
                                                               eD, lane, acc, ea, qall, pairs, pfull,
-                                                              gr, cur, e2lo);
+                                                              gr, cur, e2lo, xlo);
         else
             total += run_pass<T, NP, 1, CL, GM>(kp, tab, stab, srules, P, pass, x, e2, eD, lane, acc,
-                                                ea, qall, pairs, pfull, gr, cur, e2lo);
+                                                ea, qall, pairs, pfull, gr, cur, e2lo, xlo);
     }
     if constexpr (std::is_same<T, float>::value) {
         // the last group, if the iterations end inside it
@@ -1406,9 +1457,12 @@ __device__ __forceinline__ void bulk_partial_epilogue(const KParams &kp, int64_t
         __syncwarp();
         return;
     }
-    if (qpt < kMixedPinchQ) {
-        // next to a pinch no binary32 part is kept: every group goes to the
-        // fallback, which adds the whole sum to -G0(mu2)
+    if (qpt < kMixedPinchQ || !(sqrtf(s2) + s1 <= lim * (float)kPartialMax)) {
+        // next to a pinch, or where the estimate fails by more than
+        // kPartialMax (the badly conditioned points next to the negative
+        // real axis, whose kept groups the estimate does not bound), no
+        // binary32 part is kept: every group goes to the fallback, which adds
+        // the whole sum to -G0(mu2)
         if (lane == 0) {
             out[0] = -kp.g0mu[0];
             out[1] = -kp.g0mu[1];
