@@ -501,19 +501,21 @@ def run_gfc(args):
     def mixed_roofline(stats, secs, fallback):
         """Issue and pipe fractions of a mixed step: the binary32 bulk and the
         fallback kernel (double-float or FP64) together."""
-        if EXEC_MODEL is None:
+        if EXEC_MODEL is None or fallback != "f32x2":
             return {}
         fma_s = fp64_s = 0.0
         for s in stats:
-            nodes_fb = s.node_evals_fallback // NA
-            nodes_b = s.node_evals // NA - nodes_fb
-            eb = executed("bulk32", s.pairs_evaluated - s.pairs_fallback,
-                          s.pairs_full_table - s.pairs_full_table_fallback, nodes_b)
-            ef = executed("f32x2" if fallback == "f32x2" else "fp64", s.pairs_fallback,
-                          s.pairs_full_table_fallback, nodes_fb)
-            fma_s += fma_pipe_seconds(eb, peaks) + (fma_pipe_seconds(ef, peaks)
-                                                    if fallback == "f32x2" else 0.0)
-            fp64_s += fp64_pipe_seconds(eb, peaks) + fp64_pipe_seconds(ef, peaks)
+            # the three kernels of a mixed call: the binary32 bulk (whole
+            # points outside the cut band), the node groups re-evaluated in
+            # double-float, and the cut band in binary64
+            n_fb, n_64 = s.node_evals_fallback // NA, s.node_evals_list64 // NA
+            n_b = s.node_evals // NA - n_fb - n_64
+            pf_b = s.pairs_full_table - s.pairs_full_table_fallback - s.pairs_full_table_list64
+            eb = executed("bulk32p", s.pairs_evaluated - s.pairs_fallback - s.pairs_list64, pf_b, n_b)
+            ef = executed("nodes_df", s.pairs_fallback, s.pairs_full_table_fallback, n_fb)
+            e6 = executed("list64", s.pairs_list64, s.pairs_full_table_list64, n_64)
+            fma_s += sum(fma_pipe_seconds(e, peaks) for e in (eb, ef, e6))
+            fp64_s += sum(fp64_pipe_seconds(e, peaks) for e in (eb, ef, e6))
         T = float(sum(secs))
         return {"fma_pipe_frac": fma_s / T, "fp64_pipe_frac": fp64_s / T,
                 "peak_ffma_tflops": 2 * peaks["ffma_per_s"] / 1e12}

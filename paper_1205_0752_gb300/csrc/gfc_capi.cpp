@@ -226,6 +226,12 @@ static void tri_solve(int n, const std::vector<double> &l, const std::vector<dou
     }
 }
 
+// K of the compressed rules' thresholds rho_min(n) = exp(K / n): the n-node
+// rule's relative error ~ 10 rho^(-2n) stays below 2^-52 (binary64 and
+// double-float nodes) or 2^-26 (binary32) for rho >= rho_min(n)
+static const double kRuleK64 = 0.5 * std::log(10.0 * std::pow(2.0, 52));
+static const double kRuleK32 = 0.5 * std::log(10.0 * std::pow(2.0, 26));
+
 // Gauss rule of order n from the Jacobi matrix J of a measure of mass mu0
 // (diagonal a[0..n), off-diagonal b[0..n-1), b > 0). Nodes: the eigenvalues
 // of J, each found by bisection on the Sturm count (the number of negative
@@ -341,7 +347,7 @@ static void build_rules(Tables &T, std::vector<double> &r64, std::vector<float4>
     // thresholds: relative error ~ 10 rho^(-2n) below 2^-52 (binary64, the
     // unit roundoff: even a cancellation of 1e4 in the sums leaves ~2e-12)
     // and 2^-26 (binary32)
-    const double K64 = 0.5 * std::log(10.0 * std::pow(2.0, 52)), K32 = 0.5 * std::log(10.0 * std::pow(2.0, 26));
+    const double K64 = kRuleK64, K32 = kRuleK32;
     for (int n : ns) {
         if (n > kmax) break;
         std::vector<double> d, gam;
@@ -799,6 +805,14 @@ static void fill_kparams_tables(KParams &kp, const gfc_params *p, const Tables &
         kp.rule_n[r] = T.rule_n[r];
         kp.sig_min32[r] = (float)(0.5 * ((double)T.rho_min32[r] + 1.0 / (double)T.rho_min32[r]));
         kp.sig_min64[r] = (float)(0.5 * ((double)T.rho_min64[r] + 1.0 / (double)T.rho_min64[r]));
+    }
+    // the selection as an index: rho_min[r] = exp(K / rule_n[r]) (build_rules)
+    kp.rule_k32 = (float)kRuleK32;
+    kp.rule_k64 = (float)kRuleK64;
+    for (int m = 0; m < 128; ++m) {
+        int r = 0;
+        while (r < kp.nrule && kp.rule_n[r] < m) ++r;
+        kp.rule_idx[m] = (unsigned char)r;
     }
     kp.rules64 = T.rules64;
     kp.rules32 = T.rules32;

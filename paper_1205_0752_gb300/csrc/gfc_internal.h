@@ -117,6 +117,12 @@ struct KParams {
     int rule_off[kMaxRules], rule_n[kMaxRules];
     // (the thresholds as sigma = (rho + 1/rho)/2, which the kernels compare)
     float sig_min32[kMaxRules], sig_min64[kMaxRules];
+    // the same selection directly: rule r is exact to rounding for a node
+    // when rule_n[r] >= K / ln(rho) (rho_min[r] = exp(K / rule_n[r])), with K
+    // per arithmetic; rule_idx[m] is the first rule of at least m nodes
+    // (nrule if none)
+    float rule_k32, rule_k64;
+    unsigned char rule_idx[128];
     const double *rules64;   // per node (tau, gamma, gamma tau)
     const float4 *rules32;   // per node (tau, gamma, gamma tau, 0)
     const float2 *rules_df;  // per node (tau, gamma, gamma tau) as double-float

@@ -765,11 +765,16 @@ __device__ __forceinline__ int pair_sums(const KParams &kp, const AngTab<T, tab_
         float sig = __int_as_float(0x7f800000);
 #pragma unroll
         for (int s = 0; s < NT; ++s) sig = fminf(sig, sigma_of(to_f32(w[s].r), to_f32(w[s].i)));
-        for (int q = 0; q < kp.nrule; ++q)
-            if (sig >= sig_min<T>(kp, q)) {
-                rule = q;
-                break;
-            }
+        // rho from sigma = (rho + 1/rho)/2 (2 sigma beyond 1e4, and for an
+        // infinite sigma); the rule needs rule_n >= K/ln(rho), taken 1e-4
+        // larger: the approximate square root, logarithm and reciprocal
+        // carry relative errors of a few 1e-7 in K/ln(rho) wherever it is
+        // below 127 (ln(rho) >= 0.08); a NaN selects the full table
+        const float s2m1 = fmaxf(fmaf(sig, sig, -1.0f), 0.0f);
+        const float rho = sig > 1e4f ? 2.0f * sig : sig + s2m1 * rsqrtf(fmaxf(s2m1, 1e-30f));
+        const float nstar = (std::is_same<T, float>::value ? kp.rule_k32 : kp.rule_k64) * 1.0001f *
+                            rcp(__logf(rho));
+        rule = nstar < 127.0f ? (int)kp.rule_idx[(int)ceilf(fmaxf(nstar, 0.0f))] : kp.nrule;
         rule = __reduce_max_sync(__activemask(), rule);
     }
     if (rule < kp.nrule) {
