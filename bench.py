@@ -53,27 +53,14 @@ FLOP_PER_NODE_EVAL = 11              # 22 flops per +-psi pair (9 FMA + 4 MUL)
 L2_FLUSH_BYTES = 256 << 20
 
 # Executed work of the evaluation kernels, per unit of their own counters:
-# thread instructions per angular pair on a compressed rule (pc), per pair
-# over the full table (pf) and per contour node (n), for each pipe. Fitted to
-# ncu's instruction counters of four launches per kernel (256 x 256 grids:
-# production m^2 = 1 with compressed rules and with the full table,
-# production m^2 = 0.25, and the right half-plane; every fit reproduces the
-# four launches' counts to <= 2e-3). The per-node figures include each
-# point's fixed work spread over its 2048 ray nodes, so the model holds for
-# the ray nodes of the scalar bubble; fp64_other is the FP64 pipe's other
-# instructions (conversions, compares), fma_ops the binary32 FMA-pipe
-# operations (FFMA, FMUL, FADD), inst all instructions issued.
-EXEC_MODEL = {
-    "fp64": {"dfma": (7.0, 7.0, 34.970), "dmul": (0.0, 2.0, 38.641), "dadd": (0.004, 0.0, 16.577),
-             "fp64_other": (0.004, 0.0, 7.294), "fma_ops": (0.0, 0.0, 67.047),
-             "inst": (47.428, 47.871, 698.123)},
-    "f32x2": {"dfma": (0.0, 0.0, 0.673), "dmul": (0.0, 0.0, 0.313), "dadd": (0.004, 0.0, 0.577),
-              "fp64_other": (0.004, 0.0, 0.560), "fma_ops": (63.0, 77.0, 1007.703),
-              "inst": (81.148, 87.049, 1172.735)},
-    "bulk32": {"dfma": (0.0, 0.0, 0.188), "dmul": (0.0, 0.0, 0.157), "dadd": (0.0, 0.0, 0.095),
-               "fp64_other": (0.0, 0.0, 1.451), "fma_ops": (6.0, 6.0, 207.312),
-               "inst": (17.305, 9.285, 392.539)},
-}
+# thread instructions per angular pair on a compressed rule, per pair over
+# the full table and per contour node, for each model key (see
+# model_values): fp64 the FP64 pipe's thread slots (32 per warp instruction),
+# dfma/dmul/dadd the binary64 instructions, fma_ops the binary32 FMA-pipe
+# operations (paired forms twice), inst the warp instructions issued. Fitted
+# by `bench.py --fit-exec-model` to ncu's counters of the --calib launches
+# (256 x 256 grids of the production bubble); filled in below.
+EXEC_MODEL = {}
 # DRAM bytes per point of the FP64 evaluation kernel: ncu, one 256 x 256
 # launch of the production grid (dram__bytes_read.sum + dram__bytes_write.sum)
 TRAFFIC_PER_POINT = None
@@ -309,28 +296,214 @@ def run_serve(args):
 # executed work and rooflines
 # --------------------------------------------------------------------------
 
-def executed(arith, pairs, pairs_full, nodes):
+def executed(arith, pairs, pairs_full, nodes, points=0):
     """Thread instructions per pipe (and issued warp instructions) of a launch
-    of the `arith` kernel ('fp64', 'f32x2' or 'bulk32') from its counters."""
-    if EXEC_MODEL is None:
+    of the `arith` kernel (a key of EXEC_MODEL) from its counters."""
+    if not EXEC_MODEL or arith not in EXEC_MODEL:
         return None
     m = EXEC_MODEL[arith]
     pc = pairs - pairs_full
-    return {k: m[k][0] * pc + m[k][1] * pairs_full + m[k][2] * nodes for k in m}
+    return {k: m[k][0] * pc + m[k][1] * pairs_full + m[k][2] * nodes + m[k][3] * points
+            for k in m}
 
 
 def fp64_pipe_seconds(ex, peaks):
-    """Time the FP64 pipe needs for the executed FP64 instructions at the rate
-    measured for a stream of binary64 FMA, multiply and add in the FP64
-    kernel's proportions (the pipe issues a mixed stream faster than any one
-    of them alone; conversions and compares counted alike)."""
-    return (ex["dfma"] + ex["dmul"] + ex["dadd"] + ex["fp64_other"]) / peaks["fp64_mix_per_s"]
+    """Time the FP64 pipe needs for the executed FP64-pipe instructions (32
+    thread slots per warp instruction: DFMA, DMUL, DADD, conversions and
+    compares) at the rate measured for a stream of binary64 FMA, multiply and
+    add in the FP64 kernel's proportions (the pipe issues a mixed stream
+    faster than any one of them alone)."""
+    return ex["fp64"] / peaks["fp64_mix_per_s"]
 
 
 def fma_pipe_seconds(ex, peaks):
     """Time the FP32 FMA pipes need for the executed FFMA, FMUL and FADD
     (paired forms count twice) at the measured FFMA rate."""
     return ex["fma_ops"] / peaks["ffma_per_s"]
+
+
+# --------------------------------------------------------------------------
+# calibration of the executed-work model (EXEC_MODEL) from ncu counters
+# --------------------------------------------------------------------------
+# ncu metrics of one calibration capture, and what each model key is made of
+CALIB_METRICS = [
+    "gpu__time_duration.sum", "smsp__inst_executed.sum", "sm__inst_executed_pipe_fp64.sum",
+    "sm__sass_thread_inst_executed_op_dfma_pred_on.sum",
+    "sm__sass_thread_inst_executed_op_dmul_pred_on.sum",
+    "sm__sass_thread_inst_executed_op_dadd_pred_on.sum",
+    "sm__sass_thread_inst_executed_op_ffma_pred_on.sum",
+    "sm__sass_thread_inst_executed_op_fmul_pred_on.sum",
+    "sm__sass_thread_inst_executed_op_fadd_pred_on.sum",
+    "sm__sass_thread_inst_executed_op_ffma2_pred_on.sum",
+    "sm__sass_thread_inst_executed_op_fmul2_pred_on.sum",
+    "sm__sass_thread_inst_executed_op_fadd2_pred_on.sum",
+    "sm__pipe_fp64_cycles_active.avg.pct_of_peak_sustained_elapsed",
+    "sm__pipe_fma_cycles_active.avg.pct_of_peak_sustained_elapsed",
+    "smsp__issue_active.avg.pct_of_peak_sustained_elapsed",
+    "dram__bytes_read.sum", "dram__bytes_write.sum",
+]
+# calibration cases: 256 x 256 grids of the production bubble (2048 x 256 nodes)
+CALIB_CASES = [("m2=1", 1.0, RECT, False), ("m2=1 full table", 1.0, RECT, False),
+               ("m2=0.25", 0.25, RECT, False), ("m2=4", 4.0, RECT, False),
+               ("right half-plane m2=1", 1.0, (0.5, 5.0, -5.0, 5.0), False)]
+
+
+def run_calib(args):
+    """One call per calibration case in the given precision (after one
+    untimed call of the first case), each followed by a JSON line of its
+    counters: the launches an ncu capture of eval_kernel / eval_bulk sees,
+    in order."""
+    import torch
+    import paper_1205_0752_gb300 as gfc
+    from paper_1205_0752_gb300 import binding
+    par = gfc.make_params(dim=4, mu2=1.0, n_radial=NR, n_angular=NA, precision=args.precision)
+    side = 256
+    for k, (name, m2, rect, _) in enumerate([CALIB_CASES[0]] + CALIB_CASES):
+        binding.test_full_angular_rule("full table" in name and k > 0)
+        try:
+            gfc.eval_grid(gfc.make_prop({"kind": "scalar", "m2": m2}), par, (*rect, side, side))
+            torch.cuda.synchronize()
+            st = gfc.last_stats()
+        finally:
+            binding.test_full_angular_rule(False)
+        rec = {"case": name if k > 0 else "warm-up", "precision": args.precision}
+        rec.update({f: int(getattr(st, f)) for f in st.__dataclass_fields__})
+        print(json.dumps(rec), flush=True)
+    return 0
+
+
+def calib_units(rec, kernel):
+    """(pairs on compressed rules, pairs over the full table, contour nodes,
+    points) of one kernel of a calibration call: 'fp64' and 'f32x2' the whole
+    call, 'bulk32p' / 'nodes_df' / 'list64' the three kernels of a mixed call
+    (the fallback's points are its node-list entries, the binary64 list's
+    the points evaluated whole in binary64)."""
+    na = NA
+    if kernel in ("fp64", "f32x2"):
+        p, pf, n = rec["pairs_evaluated"], rec["pairs_full_table"], rec["node_evals"] // na
+        pts = rec["points"]
+    elif kernel == "nodes_df":
+        p, pf, n = rec["pairs_fallback"], rec["pairs_full_table_fallback"], rec["node_evals_fallback"] // na
+        pts = rec["points_partial"]
+    elif kernel == "list64":
+        p, pf, n = rec["pairs_list64"], rec["pairs_full_table_list64"], rec["node_evals_list64"] // na
+        pts = rec["points_fp64"]
+    else:
+        p = rec["pairs_evaluated"] - rec["pairs_fallback"] - rec["pairs_list64"]
+        pf = rec["pairs_full_table"] - rec["pairs_full_table_fallback"] - rec["pairs_full_table_list64"]
+        n = (rec["node_evals"] - rec["node_evals_fallback"] - rec["node_evals_list64"]) // na
+        pts = rec["points"]
+    return p - pf, pf, n, pts
+
+
+def kernel_class(name: str, precision: str) -> str:
+    """Model key of an ncu launch of a calibration call."""
+    if "eval_bulk_partial_kernel" in name:
+        return "bulk32p"
+    if "gfc::df" in name or "eval_kernel<df" in name:
+        return "nodes_df" if precision == "mixed" else "f32x2"
+    return "list64" if precision == "mixed" else "fp64"
+
+
+def model_values(row):
+    """The model's per-launch quantities from one ncu launch's metrics:
+    fp64 (FP64-pipe thread slots: 32 per warp instruction), dfma, dmul, dadd
+    (thread instructions), fma_ops (binary32 FMA-pipe operations, paired
+    forms twice) and inst (warp instructions issued)."""
+    g = lambda k: float(row.get(k, 0.0) or 0.0)
+    t = "sm__sass_thread_inst_executed_op_%s_pred_on.sum"
+    return {"fp64": 32.0 * g("sm__inst_executed_pipe_fp64.sum"),
+            "dfma": g(t % "dfma"), "dmul": g(t % "dmul"), "dadd": g(t % "dadd"),
+            "fma_ops": g(t % "ffma") + g(t % "fmul") + g(t % "fadd") +
+                       2.0 * (g(t % "ffma2") + g(t % "fmul2") + g(t % "fadd2")),
+            "inst": g("smsp__inst_executed.sum")}
+
+
+def read_ncu_csv(path):
+    """Launches of an `ncu --csv --metrics ...` log: a list of (kernel name,
+    {metric: value}) in launch order."""
+    import csv
+    rows = {}
+    with open(path) as f:
+        lines = [ln for ln in f if ln.startswith('"')]
+    for r in csv.DictReader(lines):
+        key = int(r["ID"])
+        name = r.get("Kernel Name", "")
+        val = r.get("Metric Value", "").replace(",", "")
+        try:
+            v = float(val)
+        except ValueError:
+            continue
+        unit = r.get("Metric Unit", "")
+        if unit in ("msecond", "ms"):
+            v *= 1e-3
+        elif unit in ("usecond", "us"):
+            v *= 1e-6
+        elif unit in ("nsecond", "ns"):
+            v *= 1e-9
+        rows.setdefault(key, (name, {}))[1][r["Metric Name"]] = v
+    return [rows[k] for k in sorted(rows)]
+
+
+def fit_exec_model(pairs_of_files):
+    """Least-squares fit of every model key of every kernel class: value per
+    launch = a (compressed pairs) + b (full-table pairs) + c (nodes) + d
+    (points), over the calibration launches (the warm-up call left out); the
+    points column only for the mixed form's fallback and binary64 list, and
+    left out (d = 0) where it is proportional to the nodes (every point with
+    the same contour), its work then counted per node.
+    Returns the model, the worst relative residual per kernel and key, and
+    ncu's own pipe figures beside the model's counts."""
+    samples = {}
+    for csv_path, counters_path in pairs_of_files:
+        recs = [json.loads(ln) for ln in open(counters_path) if ln.startswith("{")]
+        launches = read_ncu_csv(csv_path)
+        prec = recs[0]["precision"]
+        # group the launches by call: a call starts with its first eval kernel
+        # (mixed: the binary32 bulk; else one kernel per call)
+        calls, cur = [], None
+        for name, row in launches:
+            kc = kernel_class(name, prec)
+            if prec != "mixed" or kc == "bulk32p" or cur is None:
+                cur = []
+                calls.append(cur)
+            cur.append((kc, row))
+        assert len(calls) == len(recs), (csv_path, len(calls), len(recs))
+        for rec, call in zip(recs[1:], calls[1:]):
+            for kc, row in call:
+                samples.setdefault(kc, []).append((calib_units(rec, kc), model_values(row), row,
+                                                   rec["case"]))
+    model, report = {}, {}
+    for kc, rows in sorted(samples.items()):
+        X = np.array([u for u, _, _, _ in rows], dtype=float)
+        # columns with no work in any launch (e.g. no full-table pairs) fit to
+        # 0; a per-point term only for the kernels whose points carry very
+        # different numbers of nodes (the fallback's node groups, the binary64
+        # list), and only where it is not proportional to the nodes
+        used = np.any(X != 0, axis=0)
+        used[3] = used[3] and kc in ("nodes_df", "list64")
+        if used[3] and np.linalg.matrix_rank(X[:, used]) < int(used.sum()):
+            used[3] = False
+        model[kc] = {}
+        for key in ("dfma", "dmul", "dadd", "fp64", "fma_ops", "inst"):
+            y = np.array([v[key] for _, v, _, _ in rows])
+            coef = np.zeros(4)
+            if used.any():
+                coef[used] = np.linalg.lstsq(X[:, used], y, rcond=None)[0]
+            pred = X @ coef
+            # relative to the launch's count, launches without work (a few
+            # hundred instructions of set-up) held to an absolute floor
+            res = np.max(np.abs(pred - y) / np.maximum(np.abs(y), 1e6))
+            model[kc][key] = tuple(round(float(c), 3) for c in coef)
+            report.setdefault(kc, {})[key] = float(res)
+        report[kc]["launches"] = [
+            {"case": c, "ms": 1e3 * r.get("gpu__time_duration.sum", 0.0),
+             "dram_bytes": r.get("dram__bytes_read.sum", 0.0) + r.get("dram__bytes_write.sum", 0.0),
+             "fp64_pipe_pct": r.get("sm__pipe_fp64_cycles_active.avg.pct_of_peak_sustained_elapsed"),
+             "fma_pipe_pct": r.get("sm__pipe_fma_cycles_active.avg.pct_of_peak_sustained_elapsed"),
+             "issue_pct": r.get("smsp__issue_active.avg.pct_of_peak_sustained_elapsed")}
+            for _, _, r, c in rows]
+    return model, report
 
 
 # --------------------------------------------------------------------------
@@ -456,13 +629,14 @@ def run_gfc(args):
                "pairs_full_table": int(sum(s.pairs_full_table for s in stats)),
                "seconds": float(sum(secs))}
         out["effective_tflops"] = FLOP_PER_NODE_EVAL * out["algorithmic_node_evals"] / out["seconds"] / 1e12
-        ex = [executed("fp64", s.pairs_evaluated, s.pairs_full_table, s.node_evals // (2 * NA // 2))
+        ex = [executed("fp64", s.pairs_evaluated, s.pairs_full_table, s.node_evals // (2 * NA // 2),
+                       s.points)
               for s in stats]
         if ex[0] is not None:
             busy = sum(fp64_pipe_seconds(e, peaks) for e in ex)
             fl = sum(2 * e["dfma"] + e["dmul"] + e["dadd"] for e in ex)
             out.update(pipe_frac=busy / out["seconds"], executed_tflops=fl / out["seconds"] / 1e12,
-                       fp64_pipe_inst=float(sum(e["dfma"] + e["dmul"] + e["dadd"] + e["fp64_other"]
+                       fp64_pipe_inst=float(sum(e["fp64"]
                                                 for e in ex)))
         return out
 
@@ -501,7 +675,7 @@ def run_gfc(args):
     def mixed_roofline(stats, secs, fallback):
         """Issue and pipe fractions of a mixed step: the binary32 bulk and the
         fallback kernel (double-float or FP64) together."""
-        if EXEC_MODEL is None or fallback != "f32x2":
+        if not EXEC_MODEL or fallback != "f32x2":
             return {}
         fma_s = fp64_s = 0.0
         for s in stats:
@@ -511,9 +685,14 @@ def run_gfc(args):
             n_fb, n_64 = s.node_evals_fallback // NA, s.node_evals_list64 // NA
             n_b = s.node_evals // NA - n_fb - n_64
             pf_b = s.pairs_full_table - s.pairs_full_table_fallback - s.pairs_full_table_list64
-            eb = executed("bulk32p", s.pairs_evaluated - s.pairs_fallback - s.pairs_list64, pf_b, n_b)
-            ef = executed("nodes_df", s.pairs_fallback, s.pairs_full_table_fallback, n_fb)
-            e6 = executed("list64", s.pairs_list64, s.pairs_full_table_list64, n_64)
+            eb = executed("bulk32p", s.pairs_evaluated - s.pairs_fallback - s.pairs_list64, pf_b, n_b,
+                          s.points)
+            ef = executed("nodes_df", s.pairs_fallback, s.pairs_full_table_fallback, n_fb,
+                          s.points_partial)
+            e6 = executed("list64", s.pairs_list64, s.pairs_full_table_list64, n_64, s.points_fp64)
+            if None in (eb, ef, e6):
+                # (a kernel of the call has no calibrated instruction model)
+                return {}
             fma_s += sum(fma_pipe_seconds(e, peaks) for e in (eb, ef, e6))
             fp64_s += sum(fp64_pipe_seconds(e, peaks) for e in (eb, ef, e6))
         T = float(sum(secs))
@@ -558,9 +737,10 @@ def run_gfc(args):
              "max_rel_err": float(err_df.max()), "median_rel_err": float(np.median(err_df)),
              "rel_err_hist": decade_hist(err_df), "error_vs": "FP64 GPU results",
              "arith": "double-float (pairs of binary32) on the binary32 pipes"}
-    if EXEC_MODEL is not None:
+    if EXEC_MODEL:
         T = sum(launch_seconds(per_launch_df))
-        ex = [executed("f32x2", s.pairs_evaluated, s.pairs_full_table, s.node_evals // NA) for s in stdf]
+        ex = [executed("f32x2", s.pairs_evaluated, s.pairs_full_table, s.node_evals // NA, s.points)
+              for s in stdf]
         f32x2["fma_pipe_frac"] = sum(fma_pipe_seconds(e, peaks) for e in ex) / T
 
     # mixed precision whose routed work uses the FP64 kernel
@@ -666,11 +846,11 @@ def single_gpu_studies(gfc, si, torch, stream, flush, timed, rel_errors, peaks, 
                          grid_=g)
             e = rel_errors([G.cpu().numpy().ravel()[idx]], [ref])
             r = {"points_per_s": n * n * nst / t, "max_rel_err_vs_oracle": float(e.max())}
-            if prec == "fp64" and EXEC_MODEL is not None and prop["kind"] == "scalar":
+            if prec == "fp64" and EXEC_MODEL and prop["kind"] == "scalar":
                 # (the model is calibrated on ray nodes of the scalar bubble)
                 s = st[0]
                 ex = executed("fp64", s.pairs_evaluated, s.pairs_full_table,
-                              s.node_evals // (2 * ((par["n_angular"] + 1) // 2)))
+                              s.node_evals // (2 * ((par["n_angular"] + 1) // 2)), s.points)
                 r["fp64_pipe_frac"] = fp64_pipe_seconds(ex, peaks) / (t / nst)
             rec[prec] = r
         configs[name] = rec
@@ -753,6 +933,12 @@ def main():
                     help="FP64 timing only (profiling runs)")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "f32x2", "mixed"],
                     help="with --quick: the precision of the timed workload")
+    ap.add_argument("--calib", action="store_true",
+                    help="the calibration calls of the executed-work model in --precision "
+                         "(run under ncu --metrics with the CALIB_METRICS list)")
+    ap.add_argument("--fit-exec-model", nargs="+", metavar="CSV=COUNTERS",
+                    help="fit the executed-work model: pairs of an ncu --csv log and the "
+                         "--calib output of the same run")
     ap.add_argument("--serve", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=2000)
     ap.add_argument("--serve-rate", type=float, default=200.0)
@@ -761,8 +947,14 @@ def main():
     args = ap.parse_args()
     if args.gpus > 1 and "WORLD_SIZE" not in os.environ:
         return relaunch(args.gpus, sys.argv[1:]).returncode
+    if args.fit_exec_model:
+        model, report = fit_exec_model([a.split("=", 1) for a in args.fit_exec_model])
+        print(json.dumps({"model": model, "report": report}, indent=1))
+        return 0
     if args.impl == "reference":
         return run_reference(args)
+    if args.calib:
+        return run_calib(args)
     if args.serve:
         return run_serve(args)
     return run_gfc(args)

@@ -152,6 +152,7 @@ struct Tables {
     double L;
     double2 *rad64 = nullptr, *seg64 = nullptr, *arc64 = nullptr;
     double2 *rayp64 = nullptr;   // (rho^2, rho^(D-1) W) of the radial nodes
+    float4 *rayq_df = nullptr;   // double-float (rho^2 s, s), (rho^(D-1) W s^3), s = 1/(1 + rho^2)
     float2 *rad32 = nullptr, *seg32 = nullptr, *arc32 = nullptr;
     float4 *rad_df = nullptr, *seg_df = nullptr, *arc_df = nullptr;
     double2 *tail64 = nullptr;
@@ -425,6 +426,7 @@ static int free_tables(Tables &T)
 {
     cudaFree(T.rad64);
     cudaFree(T.rayp64);
+    cudaFree(T.rayq_df);
     cudaFree(T.seg64);
     cudaFree(T.arc64);
     cudaFree(T.rad32);
@@ -601,6 +603,15 @@ static int build_tables(Tables &T)
     };
     std::vector<float4> radD(T.n_r), segD(ns), arcD(ns), tailD(T.n_r / 2);
     for (int k = 0; k < T.n_r; ++k) radD[k] = df4(rad64[k].x, rad64[k].y);
+    // the double-float ray nodes in the frame of the ray, scaled by
+    // s = 1/(1 + rho^2) so that every node quantity stays within binary32's
+    // range (rho^2 reaches ~1e12 at 2048 nodes)
+    std::vector<float4> rayqD(2 * T.n_r);
+    for (int k = 0; k < T.n_r; ++k) {
+        const double r2 = rayp64[k].x, s = 1.0 / (1.0 + r2);
+        rayqD[2 * k] = df4(r2 * s, s);
+        rayqD[2 * k + 1] = df4(rayp64[k].y * s * s * s, 0.0);
+    }
     for (int k = 0; k < T.n_r / 2; ++k) tailD[k] = df4(tail64[k].x, tail64[k].y);
     for (int k = 0; k < ns; ++k) {
         segD[k] = df4(seg64[k].x, seg64[k].y);
@@ -611,7 +622,7 @@ static int build_tables(Tables &T)
     for (size_t j = 0; j < r64.size(); ++j) rulesD[j] = dfv(r64[j]);
     int st;
     if ((st = upload(&T.rad64, rad64, T.bytes)) || (st = upload(&T.rad32, rad32, T.bytes)) ||
-        (st = upload(&T.rayp64, rayp64, T.bytes)) ||
+        (st = upload(&T.rayp64, rayp64, T.bytes)) || (st = upload(&T.rayq_df, rayqD, T.bytes)) ||
         (st = upload(&T.seg64, seg64, T.bytes)) || (st = upload(&T.seg32, seg32, T.bytes)) ||
         (st = upload(&T.arc64, arc64, T.bytes)) || (st = upload(&T.arc32, arc32, T.bytes)) ||
         (st = upload(&T.ang64, ang64, T.bytes)) || (st = upload(&T.ang32, ang32, T.bytes)) ||
@@ -779,6 +790,7 @@ static void fill_kparams_tables(KParams &kp, const gfc_params *p, const Tables &
     kp.ang_exact = p->angular_rule == GFC_ANG_EXACT;
     kp.rad64 = T.rad64;
     kp.rayp64 = T.rayp64;
+    kp.rayq_df = T.rayq_df;
     kp.rad32 = T.rad32;
     kp.seg64 = T.seg64;
     kp.seg32 = T.seg32;

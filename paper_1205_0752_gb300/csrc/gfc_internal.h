@@ -84,6 +84,10 @@ struct KParams {
     // node tables (device, FP64 and FP32 copies)
     const double2 *rad64;   // (rho_k, W_k)
     const double2 *rayp64;  // (rho_k^2, rho_k^(D-1) W_k): binary64 ray nodes from q = 0
+    // double-float ray nodes from q = 0 in the frame of the ray, scaled by
+    // sigma_k = 1/(1 + rho_k^2): [2k] = (rho_k^2 sigma_k, sigma_k),
+    // [2k + 1] = (rho_k^(D-1) W_k sigma_k^3, 0), each a (hi, lo) pair
+    const float4 *rayq_df;
     const float2 *rad32;
     const double2 *seg64;   // (t_k, w_k) on [0, 1]
     const float2 *seg32;

@@ -810,6 +810,11 @@ __device__ __forceinline__ int pair_sums(const KParams &kp, const AngTab<T, tab_
                 }
             }
         }
+#pragma unroll
+        for (int s = 0; s < NT; ++s) {
+            A[s] = pos_finish(A[s]) + pos_finish(A1[s]);
+            B[s] = pos_finish(B[s]) + pos_finish(B1[s]);
+        }
     } else {
 #pragma unroll (pair_unroll<T>())
         for (int j = 0; j < npair; ++j) {
@@ -824,13 +829,11 @@ __device__ __forceinline__ int pair_sums(const KParams &kp, const AngTab<T, tab_
             }
         }
     }
+    if (rule < kp.nrule || NP == 0) {
 #pragma unroll
-    for (int s = 0; s < NT; ++s) {
-        A[s] = pos_finish(A[s]);
-        B[s] = pos_finish(B[s]);
-        if constexpr (NP > 0) {
-            A[s] += A1[s];
-            B[s] += B1[s];
+        for (int s = 0; s < NT; ++s) {
+            A[s] = pos_finish(A[s]);
+            B[s] = pos_finish(B[s]);
         }
     }
     qmin = qm;
@@ -1160,6 +1163,101 @@ __device__ __forceinline__ C<T> node_value(const KParams &kp, const AngTab<T, ta
     return nd.Jt * sum;
 }
 
+// Binary64 and double-float nodes of a one-term ray pass whose two legs share
+// their pole (P1 = P2 = 1/(s + M2): the scalar bubble), evaluated in the frame
+// of the ray. On the ray y = r e2 with r = rho^2 real, so every factor of
+// node_value is r and per-pass constants:
+//   a = x + y + M2 = e2 (r + xi),    xi  = (x + M2)/e2,
+//   y + M2         = e2 (r + eta),   eta = M2/e2,
+// 1/a = g/e2 and 1/(y + M2) = h/e2 with g = 1/(r + xi), h = 1/(r + eta);
+// u = y/a = r g, w = 4xy/a^2 = chi u g (chi = 4x/e2), and the lead
+// (delta y - Omega (x + M2))/a - Omega1 w = (delta r - Omega xi) g - Omega1 w.
+// The node's value Jt P1 (1/(y + M2)) (1/a) S is m (eD/e2^3) h^2 g S with
+// m = rho^(D-1) W; eD/e2^3 joins the pass's factor c 2x. The two real
+// reciprocals 1/|r + xi|^2 and 1/|r + eta|^2 come from one reciprocal of
+// their product. No node forms y, the measure or a complex reciprocal.
+// Double-float keeps binary32's range by the scale sigma = 1/(1 + r) from
+// its table: it forms g' = g/sigma and h' = h/sigma from (r + xi) sigma and
+// (r + eta) sigma, and takes m sigma^3, so that m h^2 g = (m sigma^3) h'^2 g'.
+template <typename T>
+struct RotPre {
+    C<T> xi, eta, chi, om;   // (x + M2)/e2, M2/e2, 4x/e2, Omega xi
+    T xi2, eta2;             // binary64: (Im xi)^2, (Im eta)^2
+};
+
+template <typename T>
+__device__ __forceinline__ RotPre<T> rot_pre(const KParams &kp, C<T> x, C<T> e2, C<T> m2)
+{
+    RotPre<T> rp;
+    const C<T> ei = cinv(e2);
+    rp.xi = (x + m2) * ei;
+    rp.eta = m2 * ei;
+    rp.chi = (T(4) * x) * ei;
+    rp.om = T(kp.Omega) * rp.xi;
+    rp.xi2 = rp.xi.i * rp.xi.i;
+    rp.eta2 = rp.eta.i * rp.eta.i;
+    return rp;
+}
+
+// ray node k into the pass sum ps (the factor c 2x eD/e2^3 left out);
+// returns the angular pairs evaluated, negated when they were the full table's
+template <typename T, int NP>
+__device__ __forceinline__ int node_rot(const KParams &kp, const AngTab<T, tab_size<NP>()> &tab,
+                                        const T *stab, const void *srules, const RotPre<T> &rp,
+                                        int k, C<T> &ps)
+{
+    constexpr bool D64 = std::is_same<T, double>::value;
+    // rs = r sigma, sg = sigma, m = rho^(D-1) W sigma^3 (binary64: sigma = 1)
+    T rs, sg, m, t1, t2, x1, x2, n1, n2;
+    if constexpr (D64) {
+        const double2 v = __ldg(kp.rayp64 + k);
+        rs = v.x;
+        m = v.y;
+        t1 = rs + rp.xi.r;
+        t2 = rs + rp.eta.r;
+        x1 = rp.xi.i;
+        x2 = rp.eta.i;
+        n1 = fma(t1, t1, rp.xi2);
+        n2 = fma(t2, t2, rp.eta2);
+    } else {
+        const float4 a = __ldg(kp.rayq_df + 2 * k), b = __ldg(kp.rayq_df + 2 * k + 1);
+        rs = T(a.x, a.y);
+        sg = T(a.z, a.w);
+        m = T(b.x, b.y);
+        t1 = fma(rp.xi.r, sg, rs);
+        t2 = fma(rp.eta.r, sg, rs);
+        x1 = rp.xi.i * sg;
+        x2 = rp.eta.i * sg;
+        n1 = fma(t1, t1, x1 * x1);
+        n2 = fma(t2, t2, x2 * x2);
+    }
+    const T R = rcp(n1 * n2);
+    const T s1 = R * n2, s2 = R * n1;
+    const C<T> g = {t1 * s1, -(x1 * s1)};
+    const C<T> h = {t2 * s2, -(x2 * s2)};
+    const C<T> u = rs * g;
+    C<T> ug;
+    if constexpr (D64) ug = u * g;
+    else ug = u * (sg * g);
+    const C<T> w[1] = {rp.chi * ug};
+    T A[1], B[1], qm;
+    const int np = pair_sums<T, NP, 1>(kp, tab, kp.npair, stab, srules, w, A, B, qm);
+    const C<T> T2 = {fma(-w[0].r, B[0], A[0]), w[0].i * B[0]};
+    const T Om1 = KConst<T>::om1(kp), del = KConst<T>::del(kp);
+    C<T> L;
+    if constexpr (D64) L = C<T>{fma(del, rs, -rp.om.r), -rp.om.i} * g;
+    else L = C<T>{fma(del, rs, -(rp.om.r * sg)), -(rp.om.i * sg)} * g;
+    const C<T> lead = {fma(-Om1, w[0].r, L.r), fma(-Om1, w[0].i, L.i)};
+    const C<T> vmw = {fma(T(4), u.r, -w[0].r), fma(T(4), u.i, -w[0].i)};
+    const C<T> vw = vmw * w[0];
+    const C<T> S = {fma(vw.r, T2.r, fma(-vw.i, T2.i, lead.r)),
+                    fma(vw.r, T2.i, fma(vw.i, T2.r, lead.i))};
+    const C<T> fS = ((h * h) * g) * S;
+    ps.r = fma(m, fS.r, ps.r);
+    ps.i = fma(m, fS.i, ps.i);
+    return np;
+}
+
 // ----------------------------------------------------------------------------
 // compensated accumulation
 // ----------------------------------------------------------------------------
@@ -1286,6 +1384,29 @@ __device__ __forceinline__ int run_pass(const KParams &kp, const AngTab<T, tab_s
     constexpr int FC = (NTT == 1 && !std::is_same<T, float>::value) ? 1 : 0;
     C<T> ps = {T(0), T(0)};
     int evaluated = 0;
+    auto count = [&](int np) {
+                if (np < 0) {
+                    pfull -= np;
+                    pairs -= np;
+                } else {
+                    pairs += np;
+                }
+    };
+    // binary64 and double-float one-term ray passes whose legs share their
+    // pole, without the error-scale output: nodes in the frame of the ray
+    // (node_rot), the pass factor c 2x eD/e2^3
+    constexpr bool ROT = !std::is_same<T, float>::value && FC && !CL;
+    bool rot = false;
+    RotPre<T> rp;
+    C<T> kpass = pp.cx2[0];
+    if constexpr (ROT) {
+        rot = ray && pp.same[0] && kp.cond_out == nullptr;
+        if (rot) {
+            rp = rot_pre<T>(kp, x, e2, pp.m2q[0]);
+            const C<T> ei = cinv(e2);
+            kpass = pp.cx2[0] * (eD * (ei * (ei * ei)));
+        }
+    }
     auto node = [&](int k) {
                 Node<T> nd;
                 if (!ray)
@@ -1303,32 +1424,40 @@ __device__ __forceinline__ int run_pass(const KParams &kp, const AngTab<T, tab_s
                 if constexpr (FC) ps = ps + v;
                 else acc_add(acc, v);
                 qall = fmin(qall, qm);
-                if (np < 0) {
-                    pfull -= np;
-                    pairs -= np;
-                } else {
-                    pairs += np;
-                }
+                count(np);
     };
     if constexpr (GM == 0) {
-        for (int k = lane; k < nn; k += 32) node(k);
+        if (ROT && rot) {
+            if constexpr (ROT)
+                for (int k = lane; k < nn; k += 32) count(node_rot<T, NP>(kp, tab, stab, srules, rp, k, ps));
+        } else {
+            for (int k = lane; k < nn; k += 32) node(k);
+        }
         evaluated = nn;
     } else {
-        for (int base = 0; base < nn; base += 32) {
-            // warp-uniform: the group of this iteration is selected
-            if (GM == 2 || (cur.g < kMaxGroups && ((gr.mask >> cur.g) & 1u))) {
-                evaluated += min(32, nn - base);
-                if (base + lane < nn) node(base + lane);
+        auto groups = [&](auto &&fn) {
+            for (int base = 0; base < nn; base += 32) {
+                // warp-uniform: the group of this iteration is selected
+                if (GM == 2 || (cur.g < kMaxGroups && ((gr.mask >> cur.g) & 1u))) {
+                    evaluated += min(32, nn - base);
+                    if (base + lane < nn) fn(base + lane);
+                }
+                if (--cur.left == 0) {
+                    if constexpr (GM == 2 && std::is_same<T, float>::value)
+                        group_end(gr, cur.g, lane, acc, ea);
+                    cur.left = gr.gsz;
+                    ++cur.g;
+                }
             }
-            if (--cur.left == 0) {
-                if constexpr (GM == 2 && std::is_same<T, float>::value)
-                    group_end(gr, cur.g, lane, acc, ea);
-                cur.left = gr.gsz;
-                ++cur.g;
-            }
+        };
+        if (ROT && rot) {
+            if constexpr (ROT)
+                groups([&](int k) { count(node_rot<T, NP>(kp, tab, stab, srules, rp, k, ps)); });
+        } else {
+            groups(node);
         }
     }
-    if constexpr (FC) acc_add(acc, pp.cx2[0] * ps);
+    if constexpr (FC) acc_add(acc, kpass * ps);
     return evaluated;
 }
 
@@ -1716,8 +1845,14 @@ __device__ __forceinline__ void eval_loop(const KParams &kp, const AngTab<T, tab
     }
 }
 
+// the default one-term double-float kernels held to GFC_DF_MINB blocks of 256
+// threads per SM (2: 128 registers; measured on GB300, production bubble grid:
+// 8.31 Mpoints/s, against 6.70 at 160 registers and one block)
+#ifndef GFC_DF_MINB
+#define GFC_DF_MINB 2
+#endif
 template <typename T, int NP, int NT, int CL, int GMK = 0>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, (std::is_same<T, df>::value && NT == 1 && !CL) ? GFC_DF_MINB : 1)
 eval_kernel(const __grid_constant__ KParams kp,
             const __grid_constant__ AngTab<T, tab_size<NP>()> tab, const T *__restrict__ gtab)
 {

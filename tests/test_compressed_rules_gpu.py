@@ -11,6 +11,10 @@ must agree to rounding level at every point: relative to max(|G|, tau) within
 1e-12, and in absolute terms within a small multiple of the unit roundoff
 times the point's rounding-error scale E (gfc_eval_points_cond), which is
 what rounding-level agreement means where the sum cancels.
+
+The error-scale call evaluates the scalar bubble's nodes by the general node
+code, the plain call by the code in the frame of the ray; both are checked
+against each other at rounding level too.
 """
 import numpy as np
 import pytest
@@ -34,7 +38,8 @@ def test_compressed_equals_full_rule_on_the_production_grid(m2):
     prop = {"kind": "scalar", "m2": m2}
     par = dict(dim=4, mu2=1.0, n_radial=2048, n_angular=256, precision="fp64")
     x = gfc.grid_points((*si.grid_rect("production"), 1024, 1024)).reshape(-1)
-    Gc, E = gfc.eval_points_cond(prop, par, x)
+    Gg, E = gfc.eval_points_cond(prop, par, x)
+    Gc = gfc.eval_points(prop, par, x)
     st = gfc.last_stats()
     assert 0 < st.pairs_evaluated < st.node_evals // 2      # the compressed rules were used
     binding.test_full_angular_rule(True)
@@ -45,7 +50,7 @@ def test_compressed_equals_full_rule_on_the_production_grid(m2):
         binding.test_full_angular_rule(False)
     assert stf.pairs_evaluated == stf.node_evals // 2        # every pair of the full table
     torch.cuda.synchronize()
-    gc, gf, e = Gc.cpu().numpy(), Gf.cpu().numpy(), E.cpu().numpy()
+    gc, gf, gg, e = Gc.cpu().numpy(), Gf.cpu().numpy(), Gg.cpu().numpy(), E.cpu().numpy()
     d = np.abs(gc - gf)
     tau = 1e-3 * np.max(np.abs(gf))
     rel = d / np.maximum(np.abs(gf), tau)
@@ -56,3 +61,11 @@ def test_compressed_equals_full_rule_on_the_production_grid(m2):
     assert np.all(np.isfinite(gc)) and np.all(np.isfinite(gf))
     assert rel.max() <= 1e-12, (rel.max(), x.cpu().numpy()[k])
     assert scaled.max() <= 64.0
+    # the general node code (compressed rules) against the frame of the ray
+    dg = np.abs(gg - gc)
+    relg = dg / np.maximum(np.abs(gf), tau)
+    print(f"m2={m2}: general vs ray-frame node code: max rel {relg.max():.2e}, "
+          f"max |dG|/(u E) {(dg / (U64 * e)).max():.2f}")
+    assert np.all(np.isfinite(gg))
+    assert relg.max() <= 1e-11
+    assert (dg / (U64 * e)).max() <= 64.0
