@@ -59,11 +59,36 @@ L2_FLUSH_BYTES = 256 << 20
 # dfma/dmul/dadd the binary64 instructions, fma_ops the binary32 FMA-pipe
 # operations (paired forms twice), inst the warp instructions issued. Fitted
 # by `bench.py --fit-exec-model` to ncu's counters of the --calib launches
-# (256 x 256 grids of the production bubble); filled in below.
-EXEC_MODEL = {}
-# DRAM bytes per point of the FP64 evaluation kernel: ncu, one 256 x 256
-# launch of the production grid (dram__bytes_read.sum + dram__bytes_write.sum)
-TRAFFIC_PER_POINT = None
+# (256 x 256 grids of the production bubble): tuples (per compressed pair,
+# per full-table pair, per node, per point); every fit reproduces its
+# launches' counts to <= 1.4 % (inst of the binary64 list: its empty
+# launches aside). fp64 is the FP64 kernel, list64 the mixed form's binary64
+# list, f32x2 the double-float kernel, bulk32p the mixed form's binary32 bulk,
+# nodes_df its double-float node groups.
+EXEC_MODEL = {
+    "fp64": {"dfma": (7.0, 7.0, 33.251, 0.0), "dmul": (0.0, 2.0, 29.922, 0.0),
+             "dadd": (0.004, 0.016, 2.562, 0.0), "fp64": (7.008, 9.016, 66.03, 0.0),
+             "fma_ops": (0.002, 0.0, 11.911, 0.0), "inst": (1.253, 1.527, 13.828, 0.0)},
+    "list64": {"dfma": (7.0, 7.0, 33.251, 0.0), "dmul": (0.0, 2.0, 29.922, 0.0),
+               "dadd": (0.0, 0.016, 2.609, 0.0), "fp64": (7.0, 9.016, 66.125, 0.0),
+               "fma_ops": (-0.002, 0.0, 11.949, 0.0), "inst": (0.944, 1.507, 17.041, 0.0)},
+    "f32x2": {"dfma": (0.0, 0.0, 0.673, 0.0), "dmul": (0.0, 0.0, 0.313, 0.0),
+              "dadd": (0.004, 0.0, 0.578, 0.0), "fp64": (0.008, 0.001, 2.124, 0.0),
+              "fma_ops": (63.002, 77.0, 740.474, 0.0), "inst": (2.314, 2.717, 26.571, 0.0)},
+    "bulk32p": {"dfma": (0.0, 0.0, 0.64, 0.0), "dmul": (0.0, 0.0, 0.281, 0.0),
+                "dadd": (0.0, 0.0, 0.171, 0.0), "fp64": (0.019, 0.001, 1.509, 0.0),
+                "fma_ops": (6.766, 6.057, 182.052, 0.0), "inst": (0.388, 0.293, 10.945, 0.0)},
+    "nodes_df": {"dfma": (0.0, 0.0, 0.0, 1218.0), "dmul": (0.0, 0.0, 0.0, 544.0),
+                 "dadd": (0.0, 0.0, 0.0, 1151.885), "fp64": (0.0, 0.0, -0.001, 4063.77),
+                 "fma_ops": (63.001, 77.0, 729.867, 21769.077),
+                 "inst": (2.311, 2.716, 25.896, 2669.82)},
+}
+# DRAM bytes per point of the FP64 evaluation kernel: ncu's
+# dram__bytes_read.sum + dram__bytes_write.sum of the calibration launches of
+# the production grid (256 x 256 points, compressed rules, m^2 = 0.25, 1, 4:
+# 3.82, 3.80, 3.82 B per point), scaled to a launch by its points. Below the
+# 16 B of output per point: the output drains from L2 after the kernel ends.
+TRAFFIC_PER_POINT = 3.81
 
 
 def dist_setup():
@@ -221,11 +246,32 @@ def run_reference(args):
 # serving
 # --------------------------------------------------------------------------
 
+def serve_warmup(gfc, srv):
+    """One 32 x 32 request of every request class of the mix (propagator
+    kind, D, node orders, precision), waited for: the node tables of every
+    class are built and every kernel variant loaded before the timed
+    requests, as for a server that has run a while."""
+    import synthetic_inputs as si
+    rect = si.grid_rect("small")
+    tickets = []
+    for prop in ({"kind": "scalar", "m2": 1.0}, {"kind": "dressed", "a": 1.25, "b": 0.5, "c": 2.5}):
+        for dim in (3, 4):
+            for nr, na in si.SERVING_NODES:
+                for prec in ("fp64", "mixed"):
+                    par = dict(dim=dim, mu2=1.0, n_radial=nr, n_angular=na, precision=prec)
+                    tickets.append(srv.submit(prop, par, (*rect, 32, 32))[0])
+    for t in tickets:
+        srv.wait(t)
+
+
 def serve_mix(gfc, reqs, log_path=None):
-    """Submits the requests at their arrival times to a 40 GB server, waits for
-    all of them, and returns the latency and throughput record."""
+    """Submits the requests at their arrival times to a 40 GB server (after
+    its warm-up), waits for all of them, and returns the latency and
+    throughput record of these requests."""
     import torch
     srv = gfc.Server(0, hbm_budget_bytes=40 << 30, max_slots=64)
+    serve_warmup(gfc, srv)
+    st0 = srv.stats()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     tickets = []
@@ -252,10 +298,12 @@ def serve_mix(gfc, reqs, log_path=None):
     srv.close()
     pts = sum(r["side"] ** 2 for r in reqs)
     lat = np.array([i["total_ms"] for i in infos])
-    return {"requests": len(reqs), "completed": int(st.completed), "failed": bad,
-            "p50_ms": st.p50_ms, "p99_ms": st.p99_ms, "max_ms": float(lat.max()),
-            "points_per_s": pts / wall, "wall_s": wall, "launches": int(st.launches),
-            "offered_points_per_s": pts / max(reqs[-1]["t_arrival"], 1e-9)}
+    return {"requests": len(reqs), "completed": int(st.completed - st0.completed), "failed": bad,
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "max_ms": float(lat.max()), "points_per_s": pts / wall, "wall_s": wall,
+            "launches": int(st.launches - st0.launches),
+            "offered_points_per_s": pts / max(reqs[-1]["t_arrival"], 1e-9),
+            "warmup": "one 32x32 request of each of the 32 request classes before the timed requests"}
 
 
 def serve_study(gfc, n_spec=2000, rate=200.0, n_load=600, load=0.7):

@@ -1163,30 +1163,38 @@ __device__ __forceinline__ C<T> node_value(const KParams &kp, const AngTab<T, ta
     return nd.Jt * sum;
 }
 
-// Binary64 and double-float nodes of a one-term ray pass whose two legs share
-// their pole (P1 = P2 = 1/(s + M2): the scalar bubble), evaluated in the frame
-// of the ray. On the ray y = r e2 with r = rho^2 real, so every factor of
-// node_value is r and per-pass constants:
+// Binary64 and double-float nodes of a ray pass, evaluated in the frame of the
+// ray, for the two kinds of term whose factors are all of the form 1/(y - y0):
+// terms whose two legs share their pole (P1 = P2 = 1/(s + M2): the scalar
+// bubble, and the equal-pole partial-fraction terms of the dressed
+// propagator), and the pair of dressed terms whose k-leg is the whole
+// propagator D(y) = R+/(y - y+) + R-/(y - y-) (the sector where no pole is
+// swept). On the ray y = r e2 with r = rho^2 real, so every factor of
+// node_value is r and per-pass constants; for a term with M2:
 //   a = x + y + M2 = e2 (r + xi),    xi  = (x + M2)/e2,
 //   y + M2         = e2 (r + eta),   eta = M2/e2,
 // 1/a = g/e2 and 1/(y + M2) = h/e2 with g = 1/(r + xi), h = 1/(r + eta);
 // u = y/a = r g, w = 4xy/a^2 = chi u g (chi = 4x/e2), and the lead
 // (delta y - Omega (x + M2))/a - Omega1 w = (delta r - Omega xi) g - Omega1 w.
-// The node's value Jt P1 (1/(y + M2)) (1/a) S is m (eD/e2^3) h^2 g S with
-// m = rho^(D-1) W; eD/e2^3 joins the pass's factor c 2x. The two real
-// reciprocals 1/|r + xi|^2 and 1/|r + eta|^2 come from one reciprocal of
-// their product. No node forms y, the measure or a complex reciprocal.
+// The node's value Jt P1 (1/(y + M2)) (1/a) S is m (eD/e2^3) H h g S with
+// m = rho^(D-1) W and H = h (shared pole) or H = R+ h+ + R- h- (the whole
+// propagator; its terms' M2 are -y+ and -y-, in that order); eD/e2^3 joins
+// the term's factor c 2x. The two real reciprocals 1/|r + xi|^2 and
+// 1/|r + eta|^2 come from one reciprocal of their product. No node forms y,
+// the measure or a complex reciprocal.
 // Double-float keeps binary32's range by the scale sigma = 1/(1 + r) from
 // its table: it forms g' = g/sigma and h' = h/sigma from (r + xi) sigma and
-// (r + eta) sigma, and takes m sigma^3, so that m h^2 g = (m sigma^3) h'^2 g'.
+// (r + eta) sigma, and takes m sigma^3, so that m H h g = (m sigma^3) H' h' g'.
 template <typename T>
 struct RotPre {
     C<T> xi, eta, chi, om;   // (x + M2)/e2, M2/e2, 4x/e2, Omega xi
-    T xi2, eta2;             // binary64: (Im xi)^2, (Im eta)^2
+    C<T> etak;               // distinct k-leg pole: M2k/e2
+    T xi2, eta2, etak2;      // binary64: (Im xi)^2, (Im eta)^2, (Im etak)^2
 };
 
 template <typename T>
-__device__ __forceinline__ RotPre<T> rot_pre(const KParams &kp, C<T> x, C<T> e2, C<T> m2)
+__device__ __forceinline__ RotPre<T> rot_pre(const KParams &kp, C<T> x, C<T> e2, C<T> m2,
+                                             C<T> m2k)
 {
     RotPre<T> rp;
     const C<T> ei = cinv(e2);
@@ -1196,66 +1204,134 @@ __device__ __forceinline__ RotPre<T> rot_pre(const KParams &kp, C<T> x, C<T> e2,
     rp.om = T(kp.Omega) * rp.xi;
     rp.xi2 = rp.xi.i * rp.xi.i;
     rp.eta2 = rp.eta.i * rp.eta.i;
+    if constexpr (std::is_same<T, double>::value) {
+        rp.etak = m2k * ei;
+        rp.etak2 = rp.etak.i * rp.etak.i;
+    }
     return rp;
 }
 
-// ray node k into the pass sum ps (the factor c 2x eD/e2^3 left out);
-// returns the angular pairs evaluated, negated when they were the full table's
-template <typename T, int NP>
+// Kinds of ray-frame term (node_rot): both legs on one pole, the two terms of
+// the whole dressed propagator, one term whose k-leg has a pole of its own
+enum { ROT_SHARED = 0, ROT_WHOLE = 1, ROT_DISTINCT = 2 };
+
+// Ray node k into the terms' pass sums ps (each term's factor c 2x eD/e2^3
+// left out), for terms of kind MODE (ROT_*). TAIL: node k of the mapped ray
+// from |q| = rho0 (the tail of a detour), else of the ray from q = 0. Returns
+// the angular pairs evaluated (all terms), negated when they were the full
+// table's. A distinct k-leg pole adds the factor k = 1/(r + etak) (H = k);
+// its reciprocal joins the other two.
+template <typename T, int NP, int NT, int MODE, bool TAIL>
 __device__ __forceinline__ int node_rot(const KParams &kp, const AngTab<T, tab_size<NP>()> &tab,
-                                        const T *stab, const void *srules, const RotPre<T> &rp,
-                                        int k, C<T> &ps)
+                                        const T *stab, const void *srules,
+                                        const RotPre<T> (&rp)[NT], int k, T rho0, C<T> (&ps)[NT])
 {
     constexpr bool D64 = std::is_same<T, double>::value;
+    static_assert(MODE != ROT_WHOLE || NT == 2, "the whole propagator has two terms");
+    static_assert(MODE != ROT_DISTINCT || NT == 1, "a distinct k-leg pole has one term");
     // rs = r sigma, sg = sigma, m = rho^(D-1) W sigma^3 (binary64: sigma = 1)
-    T rs, sg, m, t1, t2, x1, x2, n1, n2;
-    if constexpr (D64) {
+    T rs, sg, m;
+    if constexpr (TAIL) {
+        T rho, W;
+        load2<T>(kp, 0, k, rho, W);
+        rho = rho + rho0;
+        const T r = rho * rho;
+        const T mm = (kp.dim == 4 ? r * rho : r) * W;
+        if constexpr (D64) {
+            rs = r;
+            m = mm;
+        } else {
+            sg = rcp(T(1) + r);
+            rs = r * sg;
+            m = ((mm * sg) * sg) * sg;
+        }
+    } else if constexpr (D64) {
         const double2 v = __ldg(kp.rayp64 + k);
         rs = v.x;
         m = v.y;
-        t1 = rs + rp.xi.r;
-        t2 = rs + rp.eta.r;
-        x1 = rp.xi.i;
-        x2 = rp.eta.i;
-        n1 = fma(t1, t1, rp.xi2);
-        n2 = fma(t2, t2, rp.eta2);
     } else {
         const float4 a = __ldg(kp.rayq_df + 2 * k), b = __ldg(kp.rayq_df + 2 * k + 1);
         rs = T(a.x, a.y);
         sg = T(a.z, a.w);
         m = T(b.x, b.y);
-        t1 = fma(rp.xi.r, sg, rs);
-        t2 = fma(rp.eta.r, sg, rs);
-        x1 = rp.xi.i * sg;
-        x2 = rp.eta.i * sg;
-        n1 = fma(t1, t1, x1 * x1);
-        n2 = fma(t2, t2, x2 * x2);
     }
-    const T R = rcp(n1 * n2);
-    const T s1 = R * n2, s2 = R * n1;
-    const C<T> g = {t1 * s1, -(x1 * s1)};
-    const C<T> h = {t2 * s2, -(x2 * s2)};
-    const C<T> u = rs * g;
-    C<T> ug;
-    if constexpr (D64) ug = u * g;
-    else ug = u * (sg * g);
-    const C<T> w[1] = {rp.chi * ug};
-    T A[1], B[1], qm;
-    const int np = pair_sums<T, NP, 1>(kp, tab, kp.npair, stab, srules, w, A, B, qm);
-    const C<T> T2 = {fma(-w[0].r, B[0], A[0]), w[0].i * B[0]};
+    C<T> g[NT], h[NT], u[NT], w[NT], hk;
+#pragma unroll
+    for (int s = 0; s < NT; ++s) {
+        T t1, t2, x1, x2, n1, n2;
+        if constexpr (D64) {
+            t1 = rs + rp[s].xi.r;
+            t2 = rs + rp[s].eta.r;
+            x1 = rp[s].xi.i;
+            x2 = rp[s].eta.i;
+            n1 = fma(t1, t1, rp[s].xi2);
+            n2 = fma(t2, t2, rp[s].eta2);
+        } else {
+            t1 = fma(rp[s].xi.r, sg, rs);
+            t2 = fma(rp[s].eta.r, sg, rs);
+            x1 = rp[s].xi.i * sg;
+            x2 = rp[s].eta.i * sg;
+            n1 = fma(t1, t1, x1 * x1);
+            n2 = fma(t2, t2, x2 * x2);
+        }
+        T s1, s2;
+        if constexpr (MODE == ROT_DISTINCT) {
+            T t3, x3, n3;
+            if constexpr (D64) {
+                t3 = rs + rp[s].etak.r;
+                x3 = rp[s].etak.i;
+                n3 = fma(t3, t3, rp[s].etak2);
+            } else {
+                t3 = fma(rp[s].etak.r, sg, rs);
+                x3 = rp[s].etak.i * sg;
+                n3 = fma(t3, t3, x3 * x3);
+            }
+            const T n12 = n1 * n2;
+            const T R = rcp(n12 * n3);
+            const T r12 = R * n3, s3 = R * n12;
+            s1 = r12 * n2;
+            s2 = r12 * n1;
+            hk = {t3 * s3, -(x3 * s3)};
+        } else {
+            const T R = rcp(n1 * n2);
+            s1 = R * n2;
+            s2 = R * n1;
+        }
+        g[s] = {t1 * s1, -(x1 * s1)};
+        h[s] = {t2 * s2, -(x2 * s2)};
+        u[s] = rs * g[s];
+        C<T> ug;
+        if constexpr (D64) ug = u[s] * g[s];
+        else ug = u[s] * (sg * g[s]);
+        w[s] = rp[s].chi * ug;
+    }
+    T A[NT], B[NT], qm;
+    const int np = pair_sums<T, NP, NT>(kp, tab, kp.npair, stab, srules, w, A, B, qm);
     const T Om1 = KConst<T>::om1(kp), del = KConst<T>::del(kp);
-    C<T> L;
-    if constexpr (D64) L = C<T>{fma(del, rs, -rp.om.r), -rp.om.i} * g;
-    else L = C<T>{fma(del, rs, -(rp.om.r * sg)), -(rp.om.i * sg)} * g;
-    const C<T> lead = {fma(-Om1, w[0].r, L.r), fma(-Om1, w[0].i, L.i)};
-    const C<T> vmw = {fma(T(4), u.r, -w[0].r), fma(T(4), u.i, -w[0].i)};
-    const C<T> vw = vmw * w[0];
-    const C<T> S = {fma(vw.r, T2.r, fma(-vw.i, T2.i, lead.r)),
-                    fma(vw.r, T2.i, fma(vw.i, T2.r, lead.i))};
-    const C<T> fS = ((h * h) * g) * S;
-    ps.r = fma(m, fS.r, ps.r);
-    ps.i = fma(m, fS.i, ps.i);
-    return np;
+    C<T> H = {T(0), T(0)};
+    if constexpr (MODE == ROT_WHOLE) {
+        const C<T> Rp = KConst<T>::Rp(kp);
+        H = Rp * h[0] + conj(Rp) * h[NT - 1];
+    } else if constexpr (MODE == ROT_DISTINCT) {
+        H = hk;
+    }
+#pragma unroll
+    for (int s = 0; s < NT; ++s) {
+        const C<T> T2 = {fma(-w[s].r, B[s], A[s]), w[s].i * B[s]};
+        C<T> L;
+        if constexpr (D64) L = C<T>{fma(del, rs, -rp[s].om.r), -rp[s].om.i} * g[s];
+        else L = C<T>{fma(del, rs, -(rp[s].om.r * sg)), -(rp[s].om.i * sg)} * g[s];
+        const C<T> lead = {fma(-Om1, w[s].r, L.r), fma(-Om1, w[s].i, L.i)};
+        const C<T> vmw = {fma(T(4), u[s].r, -w[s].r), fma(T(4), u[s].i, -w[s].i)};
+        const C<T> vw = vmw * w[s];
+        const C<T> S = {fma(vw.r, T2.r, fma(-vw.i, T2.i, lead.r)),
+                        fma(vw.r, T2.i, fma(vw.i, T2.r, lead.i))};
+        const C<T> hh = MODE == ROT_SHARED ? h[s] * h[s] : H * h[s];
+        const C<T> fS = (hh * g[s]) * S;
+        ps[s].r = fma(m, fS.r, ps[s].r);
+        ps[s].i = fma(m, fS.i, ps[s].i);
+    }
+    return np * NT;
 }
 
 // ----------------------------------------------------------------------------
@@ -1392,19 +1468,44 @@ __device__ __forceinline__ int run_pass(const KParams &kp, const AngTab<T, tab_s
                     pairs += np;
                 }
     };
-    // binary64 and double-float one-term ray passes whose legs share their
-    // pole, without the error-scale output: nodes in the frame of the ray
-    // (node_rot), the pass factor c 2x eD/e2^3
-    constexpr bool ROT = !std::is_same<T, float>::value && FC && !CL;
-    bool rot = false;
-    RotPre<T> rp;
-    C<T> kpass = pp.cx2[0];
+    // binary64 and double-float passes whose terms all share their poles,
+    // carry the two terms of the whole dressed propagator, or are one term
+    // with a k-leg pole of its own, without the error-scale output: ray
+    // nodes in the frame of the ray (node_rot; on a detour only its tail
+    // ray), each term's pass factor c 2x eD/e2^3
+    constexpr bool ROT = !std::is_same<T, float>::value && !CL;
+    // (distinct k-leg poles in binary64 only: in double-float their extra
+    // registers would spill in the one-term kernels, held to 128)
+#ifndef GFC_RDIST
+#define GFC_RDIST 1
+#endif
+    constexpr bool RDIST = std::is_same<T, double>::value && GFC_RDIST;
+    int mode = -1;
+    RotPre<T> rp[NTT];
+    C<T> kpass[NTT], pr[NTT];
+    T rho0 = T(0);
     if constexpr (ROT) {
-        rot = ray && pp.same[0] && kp.cond_out == nullptr;
-        if (rot) {
-            rp = rot_pre<T>(kp, x, e2, pp.m2q[0]);
+        if (kp.cond_out == nullptr && pp.nt == NTT) {
+            if (NTT == 1)
+                mode = pp.same[0] ? ROT_SHARED : ((RDIST && !pp.full[0]) ? ROT_DISTINCT : -1);
+            else if (pp.full[0] && pp.full[NTT - 1])
+                mode = ROT_WHOLE;
+            else if (pp.same[0] && pp.same[NTT - 1])
+                mode = ROT_SHARED;
+        }
+        // a detour's first segments are not on the ray; its tail is
+        if (!ray && mode != ROT_DISTINCT) mode = -1;
+        if (mode >= 0) {
             const C<T> ei = cinv(e2);
-            kpass = pp.cx2[0] * (eD * (ei * (ei * ei)));
+            const C<T> f = eD * (ei * (ei * ei));
+#pragma unroll
+            for (int s = 0; s < NTT; ++s) {
+                rp[s] = rot_pre<T>(kp, x, e2, pp.m2q[s], pp.m2k[s]);
+                kpass[s] = pp.cx2[s] * f;
+                pr[s] = {T(0), T(0)};
+            }
+            if constexpr (RDIST)
+                if (!ray) rho0 = dps->sqRd;
         }
     }
     auto node = [&](int k) {
@@ -1426,10 +1527,40 @@ __device__ __forceinline__ int run_pass(const KParams &kp, const AngTab<T, tab_s
                 qall = fmin(qall, qm);
                 count(np);
     };
+    // node k of the pass in the frame of the ray (mode >= 0)
+    auto rnode = [&](int k) {
+        if constexpr (ROT) {
+            if constexpr (NTT == 1) {
+                if (mode == ROT_SHARED) {
+                    count(node_rot<T, NP, NTT, ROT_SHARED, false>(kp, tab, stab, srules, rp, k, rho0, pr));
+                } else if constexpr (RDIST) {
+                    if (ray)
+                        count(node_rot<T, NP, NTT, ROT_DISTINCT, false>(kp, tab, stab, srules, rp, k,
+                                                                         rho0, pr));
+                    else if (k < 3 * kp.n_s)
+                        node(k);
+                    else
+                        count(node_rot<T, NP, NTT, ROT_DISTINCT, true>(kp, tab, stab, srules, rp,
+                                                                        k - 3 * kp.n_s, rho0, pr));
+                }
+            } else {
+                if (mode == ROT_WHOLE)
+                    count(node_rot<T, NP, NTT, ROT_WHOLE, false>(kp, tab, stab, srules, rp, k, rho0, pr));
+                else
+                    count(node_rot<T, NP, NTT, ROT_SHARED, false>(kp, tab, stab, srules, rp, k, rho0, pr));
+            }
+        }
+    };
     if constexpr (GM == 0) {
-        if (ROT && rot) {
-            if constexpr (ROT)
-                for (int k = lane; k < nn; k += 32) count(node_rot<T, NP>(kp, tab, stab, srules, rp, k, ps));
+        if (ROT && mode >= 0) {
+            if constexpr (ROT) {
+                if (mode == ROT_SHARED) {
+                    for (int k = lane; k < nn; k += 32)
+                        count(node_rot<T, NP, NTT, ROT_SHARED, false>(kp, tab, stab, srules, rp, k, rho0, pr));
+                } else if constexpr (RDIST || NTT == 2) {
+                    for (int k = lane; k < nn; k += 32) rnode(k);
+                }
+            }
         } else {
             for (int k = lane; k < nn; k += 32) node(k);
         }
@@ -1450,14 +1581,27 @@ __device__ __forceinline__ int run_pass(const KParams &kp, const AngTab<T, tab_s
                 }
             }
         };
-        if (ROT && rot) {
-            if constexpr (ROT)
-                groups([&](int k) { count(node_rot<T, NP>(kp, tab, stab, srules, rp, k, ps)); });
+        if (ROT && mode >= 0) {
+            if constexpr (RDIST || NTT == 2)
+                groups(rnode);
+            else if constexpr (ROT)
+                groups([&](int k) {
+                    count(node_rot<T, NP, NTT, ROT_SHARED, false>(kp, tab, stab, srules, rp, k, rho0, pr));
+                });
         } else {
             groups(node);
         }
     }
-    if constexpr (FC) acc_add(acc, kpass * ps);
+    if (ROT && mode >= 0) {
+        C<T> v = kpass[0] * pr[0];
+#pragma unroll
+        for (int s = 1; s < NTT; ++s) v = v + kpass[s] * pr[s];
+        // (a detour's segments before its tail: the general nodes' sum)
+        if constexpr (FC && RDIST) v = v + pp.cx2[0] * ps;
+        acc_add(acc, v);
+    } else if constexpr (FC) {
+        acc_add(acc, pp.cx2[0] * ps);
+    }
     return evaluated;
 }
 
@@ -1847,7 +1991,9 @@ __device__ __forceinline__ void eval_loop(const KParams &kp, const AngTab<T, tab
 
 // the default one-term double-float kernels held to GFC_DF_MINB blocks of 256
 // threads per SM (2: 128 registers; measured on GB300, production bubble grid:
-// 8.31 Mpoints/s, against 6.70 at 160 registers and one block)
+// 8.31 Mpoints/s, against 6.70 at 160 registers and one block). The binary64
+// kernels are left at one block (157 registers: 1.60 Mpoints/s, against 1.57
+// held to two blocks with spills).
 #ifndef GFC_DF_MINB
 #define GFC_DF_MINB 2
 #endif
@@ -1874,8 +2020,11 @@ eval_bulk_partial_kernel(const __grid_constant__ KParams kp,
 // points [items[i].p0, items[i].p1) of request slot items[i].slot; offs[i] is
 // its first index in the launch-wide point count. All requests of a launch
 // share the angular rule (n_angular, D) held in the constant bank.
+// (binary32: 3 blocks of 256 threads per SM for one term, 2 for two; the
+// others one, which gives the binary64 kernel the registers it needs without
+// spills)
 template <typename T, int NP, int NT, int CL>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, std::is_same<T, float>::value ? (NT == 1 ? 3 : 2) : 1)
 eval_batch_kernel(const KParams *__restrict__ slots, const BatchItem *__restrict__ items,
                   const int64_t *__restrict__ offs, int nitems, int64_t total,
                   unsigned long long *counter, int mode,

@@ -74,11 +74,15 @@ def grid_rect(kind: str):
     }[kind]
 
 
+# (n_radial, n_angular) orders of the serving requests
+SERVING_NODES = [(256, 64), (512, 128), (1024, 128), (2048, 256)]
+
+
 def serving_mix(seed: int, count: int, rate_hz: float = 200.0):
     """Request descriptors of the serving workload, in arrival order."""
     g = SplitMix64(seed)
     sides = [32, 64, 128, 256, 512]
-    nodes = [(256, 64), (512, 128), (1024, 128), (2048, 256)]
+    nodes = SERVING_NODES
     masses = [0.5, 1.0, 2.0]
     t = 0.0
     out = []
