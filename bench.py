@@ -66,29 +66,28 @@ L2_FLUSH_BYTES = 256 << 20
 # list, f32x2 the double-float kernel, bulk32p the mixed form's binary32 bulk,
 # nodes_df its double-float node groups.
 EXEC_MODEL = {
-    "fp64": {"dfma": (7.0, 7.0, 33.251, 0.0), "dmul": (0.0, 2.0, 29.922, 0.0),
-             "dadd": (0.004, 0.016, 2.562, 0.0), "fp64": (7.008, 9.016, 66.03, 0.0),
-             "fma_ops": (0.002, 0.0, 11.911, 0.0), "inst": (1.253, 1.527, 13.828, 0.0)},
-    "list64": {"dfma": (7.0, 7.0, 33.251, 0.0), "dmul": (0.0, 2.0, 29.922, 0.0),
-               "dadd": (0.0, 0.016, 2.609, 0.0), "fp64": (7.0, 9.016, 66.125, 0.0),
-               "fma_ops": (-0.002, 0.0, 11.949, 0.0), "inst": (0.944, 1.507, 17.041, 0.0)},
+    "fp64": {"dfma": (7.0, 7.0, 33.313, 0.0), "dmul": (0.0, 2.0, 27.079, 0.0),
+             "dadd": (0.004, 0.016, 2.609, 0.0), "fp64": (7.008, 9.016, 63.296, 0.0),
+             "fma_ops": (0.002, 0.0, 10.927, 0.0), "inst": (1.261, 1.528, 13.301, 0.0)},
+    "list64": {"dfma": (7.0, 7.0, 33.313, 0.0), "dmul": (0.0, 2.0, 27.079, 0.0),
+               "dadd": (0.0, 0.016, 2.656, 0.0), "fp64": (7.0, 9.016, 63.391, 0.0),
+               "fma_ops": (-0.002, 0.0, 10.965, 0.0), "inst": (0.945, 1.507, 16.584, 0.0)},
     "f32x2": {"dfma": (0.0, 0.0, 0.673, 0.0), "dmul": (0.0, 0.0, 0.313, 0.0),
               "dadd": (0.004, 0.0, 0.578, 0.0), "fp64": (0.008, 0.001, 2.124, 0.0),
-              "fma_ops": (63.002, 77.0, 740.474, 0.0), "inst": (2.314, 2.717, 26.571, 0.0)},
+              "fma_ops": (63.002, 77.0, 740.286, 0.0), "inst": (2.314, 2.716, 26.613, 0.0)},
     "bulk32p": {"dfma": (0.0, 0.0, 0.64, 0.0), "dmul": (0.0, 0.0, 0.281, 0.0),
                 "dadd": (0.0, 0.0, 0.171, 0.0), "fp64": (0.019, 0.001, 1.509, 0.0),
                 "fma_ops": (6.766, 6.057, 182.052, 0.0), "inst": (0.388, 0.293, 10.945, 0.0)},
     "nodes_df": {"dfma": (0.0, 0.0, 0.0, 1218.0), "dmul": (0.0, 0.0, 0.0, 544.0),
                  "dadd": (0.0, 0.0, 0.0, 1151.885), "fp64": (0.0, 0.0, -0.001, 4063.77),
-                 "fma_ops": (63.001, 77.0, 729.867, 21769.077),
-                 "inst": (2.311, 2.716, 25.896, 2669.82)},
+                 "fma_ops": (63.001, 77.0, 729.867, 21385.077), "inst": (2.311, 2.716, 25.927, 2681.82)},
 }
 # DRAM bytes per point of the FP64 evaluation kernel: ncu's
 # dram__bytes_read.sum + dram__bytes_write.sum of the calibration launches of
 # the production grid (256 x 256 points, compressed rules, m^2 = 0.25, 1, 4:
-# 3.82, 3.80, 3.82 B per point), scaled to a launch by its points. Below the
+# 5.11, 4.73, 4.15 B per point), scaled to a launch by its points. Below the
 # 16 B of output per point: the output drains from L2 after the kernel ends.
-TRAFFIC_PER_POINT = 3.81
+TRAFFIC_PER_POINT = 4.66
 
 
 def dist_setup():
