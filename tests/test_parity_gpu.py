@@ -169,6 +169,23 @@ def test_row_shards_equal_unsharded():
     assert np.array_equal(np.concatenate(parts), whole)
 
 
+def test_interleaved_row_shards_match_the_whole_grid():
+    """The benchmark's weak-scaling layout: rank r of N evaluates the rows
+    i = r (mod N) of an (N side) x side grid over the production rectangle
+    as a side x side grid of its own (bench.shard_rect). Each shard equals
+    those rows of the whole grid; the coordinates agree to rounding (the
+    shard's origin is computed apart), so the values agree to 1e-12."""
+    import bench
+    side, N = 16, 3
+    par = dict(dim=4, mu2=1.0, n_radial=256, n_angular=64, precision="fp64")
+    whole = run_grid(SCALAR, par, si.grid_rect("production"), N * side, side)
+    tau = 1e-3 * np.max(np.abs(whole))
+    for r in range(N):
+        part = run_grid(SCALAR, par, bench.shard_rect(r, N, side), side, side)
+        ref = whole[r::N]
+        assert np.max(np.abs(part - ref) / np.maximum(np.abs(ref), tau)) <= 1e-12, r
+
+
 @pytest.mark.parametrize("precision", ["fp64", "mixed", "f32x2"])
 @pytest.mark.parametrize("m2", [0.25, 1.0, 4.0])
 def test_production_grid_sampled(precision, m2):
