@@ -768,7 +768,12 @@ def run_gfc(args):
              "rel_err_hist": decade_hist(err),
              "error_vs": "FP64 GPU results (parity <= 1e-10 with the oracle)",
              "fallback": "double-float (f32x2)",
-             "routed_fraction_per_mass": [dict(m2=m2, points_routed=s.points_fp64 / s.points,
+             # per mass: the share of points evaluated whole in binary64 (the
+             # cut band and points next to a pinch), of points with node groups
+             # re-evaluated in double-float, and of node evaluations done in
+             # double-float
+             "routed_fraction_per_mass": [dict(m2=m2, points_binary64_whole=s.points_fp64 / s.points,
+                                               points_with_fallback_groups=s.points_partial / s.points,
                                                fallback_node_evals=s.node_evals_fallback / max(1, s.node_evals))
                                           for m2, s in zip(MASSES2, stmx)],
              "per_mass_ms": [1e3 * s for s in launch_seconds(per_launch_mx)],
