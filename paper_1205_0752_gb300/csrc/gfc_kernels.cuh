@@ -1218,11 +1218,16 @@ enum { ROT_SHARED = 0, ROT_WHOLE = 1, ROT_DISTINCT = 2 };
 // Ray node k into the terms' pass sums ps (each term's factor c 2x eD/e2^3
 // left out), for terms of kind MODE (ROT_*). TAIL: node k of the mapped ray
 // from |q| = rho0 (the tail of a detour), else of the ray from q = 0. Returns
-// the angular pairs evaluated (all terms), negated when they were the full
-// table's. A distinct k-leg pole adds the factor k = 1/(r + etak) (H = k);
-// its reciprocal joins the other two.
+// the angular pairs evaluated for each term (x: the first, y: the second),
+// negated when they were the full table's. With two terms each term's
+// angular sum takes its own compressed rule (GFC_SPLIT_RULES; else the larger
+// of the two for both). A distinct k-leg pole adds the factor k = 1/(r +
+// etak) (H = k); its reciprocal joins the other two.
+#ifndef GFC_SPLIT_RULES
+#define GFC_SPLIT_RULES 1
+#endif
 template <typename T, int NP, int NT, int MODE, bool TAIL>
-__device__ __forceinline__ int node_rot(const KParams &kp, const AngTab<T, tab_size<NP>()> &tab,
+__device__ __forceinline__ int2 node_rot(const KParams &kp, const AngTab<T, tab_size<NP>()> &tab,
                                         const T *stab, const void *srules,
                                         const RotPre<T> (&rp)[NT], int k, T rho0, C<T> (&ps)[NT])
 {
@@ -1306,7 +1311,23 @@ __device__ __forceinline__ int node_rot(const KParams &kp, const AngTab<T, tab_s
         w[s] = rp[s].chi * ug;
     }
     T A[NT], B[NT], qm;
-    const int np = pair_sums<T, NP, NT>(kp, tab, kp.npair, stab, srules, w, A, B, qm);
+    int2 np = {0, 0};
+    if constexpr (NT == 2 && GFC_SPLIT_RULES) {
+#pragma unroll
+        for (int s = 0; s < NT; ++s) {
+            const C<T> ws[1] = {w[s]};
+            T As[1], Bs[1];
+            const int n = pair_sums<T, NP, 1>(kp, tab, kp.npair, stab, srules, ws, As, Bs, qm);
+            A[s] = As[0];
+            B[s] = Bs[0];
+            if (s == 0) np.x = n;
+            else np.y = n;
+        }
+    } else {
+        const int n = pair_sums<T, NP, NT>(kp, tab, kp.npair, stab, srules, w, A, B, qm);
+        np.x = n;
+        np.y = NT == 2 ? n : 0;
+    }
     const T Om1 = KConst<T>::om1(kp), del = KConst<T>::del(kp);
     C<T> H = {T(0), T(0)};
     if constexpr (MODE == ROT_WHOLE) {
@@ -1331,7 +1352,7 @@ __device__ __forceinline__ int node_rot(const KParams &kp, const AngTab<T, tab_s
         ps[s].r = fma(m, fS.r, ps[s].r);
         ps[s].i = fma(m, fS.i, ps[s].i);
     }
-    return np * NT;
+    return np;
 }
 
 // ----------------------------------------------------------------------------
@@ -1468,6 +1489,10 @@ __device__ __forceinline__ int run_pass(const KParams &kp, const AngTab<T, tab_s
                     pairs += np;
                 }
     };
+    auto rcount = [&](int2 np) {
+        count(np.x);
+        count(np.y);
+    };
     // binary64 and double-float passes whose terms all share their poles,
     // carry the two terms of the whole dressed propagator, or are one term
     // with a k-leg pole of its own, without the error-scale output: ray
@@ -1532,22 +1557,22 @@ __device__ __forceinline__ int run_pass(const KParams &kp, const AngTab<T, tab_s
         if constexpr (ROT) {
             if constexpr (NTT == 1) {
                 if (mode == ROT_SHARED) {
-                    count(node_rot<T, NP, NTT, ROT_SHARED, false>(kp, tab, stab, srules, rp, k, rho0, pr));
+                    rcount(node_rot<T, NP, NTT, ROT_SHARED, false>(kp, tab, stab, srules, rp, k, rho0, pr));
                 } else if constexpr (RDIST) {
                     if (ray)
-                        count(node_rot<T, NP, NTT, ROT_DISTINCT, false>(kp, tab, stab, srules, rp, k,
+                        rcount(node_rot<T, NP, NTT, ROT_DISTINCT, false>(kp, tab, stab, srules, rp, k,
                                                                          rho0, pr));
                     else if (k < 3 * kp.n_s)
                         node(k);
                     else
-                        count(node_rot<T, NP, NTT, ROT_DISTINCT, true>(kp, tab, stab, srules, rp,
+                        rcount(node_rot<T, NP, NTT, ROT_DISTINCT, true>(kp, tab, stab, srules, rp,
                                                                         k - 3 * kp.n_s, rho0, pr));
                 }
             } else {
                 if (mode == ROT_WHOLE)
-                    count(node_rot<T, NP, NTT, ROT_WHOLE, false>(kp, tab, stab, srules, rp, k, rho0, pr));
+                    rcount(node_rot<T, NP, NTT, ROT_WHOLE, false>(kp, tab, stab, srules, rp, k, rho0, pr));
                 else
-                    count(node_rot<T, NP, NTT, ROT_SHARED, false>(kp, tab, stab, srules, rp, k, rho0, pr));
+                    rcount(node_rot<T, NP, NTT, ROT_SHARED, false>(kp, tab, stab, srules, rp, k, rho0, pr));
             }
         }
     };
@@ -1556,7 +1581,7 @@ __device__ __forceinline__ int run_pass(const KParams &kp, const AngTab<T, tab_s
             if constexpr (ROT) {
                 if (mode == ROT_SHARED) {
                     for (int k = lane; k < nn; k += 32)
-                        count(node_rot<T, NP, NTT, ROT_SHARED, false>(kp, tab, stab, srules, rp, k, rho0, pr));
+                        rcount(node_rot<T, NP, NTT, ROT_SHARED, false>(kp, tab, stab, srules, rp, k, rho0, pr));
                 } else if constexpr (RDIST || NTT == 2) {
                     for (int k = lane; k < nn; k += 32) rnode(k);
                 }
@@ -1586,7 +1611,7 @@ __device__ __forceinline__ int run_pass(const KParams &kp, const AngTab<T, tab_s
                 groups(rnode);
             else if constexpr (ROT)
                 groups([&](int k) {
-                    count(node_rot<T, NP, NTT, ROT_SHARED, false>(kp, tab, stab, srules, rp, k, rho0, pr));
+                    rcount(node_rot<T, NP, NTT, ROT_SHARED, false>(kp, tab, stab, srules, rp, k, rho0, pr));
                 });
         } else {
             groups(node);
