@@ -1226,6 +1226,11 @@ enum { ROT_SHARED = 0, ROT_WHOLE = 1, ROT_DISTINCT = 2 };
 #ifndef GFC_SPLIT_RULES
 #define GFC_SPLIT_RULES 1
 #endif
+// Ray-frame nodes for terms whose k-leg has a pole of its own (1), or the
+// general node code for them (0)
+#ifndef GFC_RDIST
+#define GFC_RDIST 1
+#endif
 template <typename T, int NP, int NT, int MODE, bool TAIL>
 __device__ __forceinline__ int2 node_rot(const KParams &kp, const AngTab<T, tab_size<NP>()> &tab,
                                         const T *stab, const void *srules,
@@ -1501,9 +1506,6 @@ __device__ __forceinline__ int run_pass(const KParams &kp, const AngTab<T, tab_s
     constexpr bool ROT = !std::is_same<T, float>::value && !CL;
     // (distinct k-leg poles in binary64 only: in double-float their extra
     // registers would spill in the one-term kernels, held to 128)
-#ifndef GFC_RDIST
-#define GFC_RDIST 1
-#endif
     constexpr bool RDIST = std::is_same<T, double>::value && GFC_RDIST;
     int mode = -1;
     RotPre<T> rp[NTT];
