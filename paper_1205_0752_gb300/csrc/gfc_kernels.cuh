@@ -1163,13 +1163,15 @@ __device__ __forceinline__ C<T> node_value(const KParams &kp, const AngTab<T, ta
     return nd.Jt * sum;
 }
 
-// Binary64 and double-float nodes of a ray pass, evaluated in the frame of the
-// ray, for the two kinds of term whose factors are all of the form 1/(y - y0):
+// Binary64 and double-float nodes of a ray, evaluated in the frame of the ray,
+// for the three kinds of term whose factors are all of the form 1/(y - y0):
 // terms whose two legs share their pole (P1 = P2 = 1/(s + M2): the scalar
 // bubble, and the equal-pole partial-fraction terms of the dressed
-// propagator), and the pair of dressed terms whose k-leg is the whole
-// propagator D(y) = R+/(y - y+) + R-/(y - y-) (the sector where no pole is
-// swept). On the ray y = r e2 with r = rho^2 real, so every factor of
+// propagator), the pair of dressed terms whose k-leg is the whole propagator
+// D(y) = R+/(y - y+) + R-/(y - y-) (the sector where no pole is swept), and,
+// in binary64, one term whose k-leg has a pole of its own (the complex-pair
+// legs of the paper's example; on a detour only its tail ray). On the ray
+// y = r e2 with r = rho^2 real, so every factor of
 // node_value is r and per-pass constants; for a term with M2:
 //   a = x + y + M2 = e2 (r + xi),    xi  = (x + M2)/e2,
 //   y + M2         = e2 (r + eta),   eta = M2/e2,
@@ -1177,11 +1179,12 @@ __device__ __forceinline__ C<T> node_value(const KParams &kp, const AngTab<T, ta
 // u = y/a = r g, w = 4xy/a^2 = chi u g (chi = 4x/e2), and the lead
 // (delta y - Omega (x + M2))/a - Omega1 w = (delta r - Omega xi) g - Omega1 w.
 // The node's value Jt P1 (1/(y + M2)) (1/a) S is m (eD/e2^3) H h g S with
-// m = rho^(D-1) W and H = h (shared pole) or H = R+ h+ + R- h- (the whole
-// propagator; its terms' M2 are -y+ and -y-, in that order); eD/e2^3 joins
-// the term's factor c 2x. The two real reciprocals 1/|r + xi|^2 and
-// 1/|r + eta|^2 come from one reciprocal of their product. No node forms y,
-// the measure or a complex reciprocal.
+// m = rho^(D-1) W and H = h (shared pole), H = R+ h+ + R- h- (the whole
+// propagator; its terms' M2 are -y+ and -y-, in that order) or
+// H = 1/(r + M2k/e2) (a k-leg pole M2k of its own); eD/e2^3 joins
+// the term's factor c 2x. The real reciprocals 1/|r + xi|^2 and
+// 1/|r + eta|^2 (and 1/|r + M2k/e2|^2) come from one reciprocal of their
+// product. No node forms y, the measure or a complex reciprocal.
 // Double-float keeps binary32's range by the scale sigma = 1/(1 + r) from
 // its table: it forms g' = g/sigma and h' = h/sigma from (r + xi) sigma and
 // (r + eta) sigma, and takes m sigma^3, so that m H h g = (m sigma^3) H' h' g'.
@@ -1215,14 +1218,8 @@ __device__ __forceinline__ RotPre<T> rot_pre(const KParams &kp, C<T> x, C<T> e2,
 // the whole dressed propagator, one term whose k-leg has a pole of its own
 enum { ROT_SHARED = 0, ROT_WHOLE = 1, ROT_DISTINCT = 2 };
 
-// Ray node k into the terms' pass sums ps (each term's factor c 2x eD/e2^3
-// left out), for terms of kind MODE (ROT_*). TAIL: node k of the mapped ray
-// from |q| = rho0 (the tail of a detour), else of the ray from q = 0. Returns
-// the angular pairs evaluated for each term (x: the first, y: the second),
-// negated when they were the full table's. With two terms each term's
-// angular sum takes its own compressed rule (GFC_SPLIT_RULES; else the larger
-// of the two for both). A distinct k-leg pole adds the factor k = 1/(r +
-// etak) (H = k); its reciprocal joins the other two.
+// Two-term ray passes: each term's angular sum on its own compressed rule
+// (1), or both on the larger of the two (0)
 #ifndef GFC_SPLIT_RULES
 #define GFC_SPLIT_RULES 1
 #endif
@@ -1231,6 +1228,12 @@ enum { ROT_SHARED = 0, ROT_WHOLE = 1, ROT_DISTINCT = 2 };
 #ifndef GFC_RDIST
 #define GFC_RDIST 1
 #endif
+
+// Ray node k into the terms' pass sums ps (each term's factor c 2x eD/e2^3
+// left out), for terms of kind MODE (ROT_*). TAIL: node k of the mapped ray
+// from |q| = rho0 (the tail of a detour), else of the ray from q = 0. Returns
+// the angular pairs evaluated for each term (x: the first, y: the second),
+// negated when they were the full table's.
 template <typename T, int NP, int NT, int MODE, bool TAIL>
 __device__ __forceinline__ int2 node_rot(const KParams &kp, const AngTab<T, tab_size<NP>()> &tab,
                                         const T *stab, const void *srules,
