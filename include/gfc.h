@@ -41,7 +41,7 @@ extern "C" {
 #endif
 
 #define GFC_VERSION_MAJOR 1
-#define GFC_VERSION_MINOR 5
+#define GFC_VERSION_MINOR 6
 
 enum {
     GFC_OK = 0,
@@ -438,8 +438,46 @@ typedef struct {
 /* GFC_ENOTFOUND for an unknown ticket. */
 int gfc_server_request_info(gfc_server *s, uint64_t ticket, gfc_request_info *out);
 
+/* Estimated work the server has not launched yet (queued and admitted
+ * requests), in its scheduling units (binary32 angular pair evaluations; a
+ * binary64 pair counts 24, a double-float pair 6). */
+int gfc_server_load(gfc_server *s, double *work);
+
 /* Cancels what is still queued, drains what is on the device, frees all. */
 int gfc_server_destroy(gfc_server *s);
+
+/* ------------------------------------------------------------------------ */
+/* Several devices: one server per device, each request handed whole to the  */
+/* server with the least estimated work outstanding. Every grid point is     */
+/* independent (Sect. 1), so a request needs nothing from the other devices. */
+/* ------------------------------------------------------------------------ */
+
+typedef struct gfc_router gfc_router;
+
+/* One server per entry of devices[0..ndevices) (1 <= ndevices <= 256; an
+ * entry may repeat), each with the given budget and slots as for
+ * gfc_server_create. */
+int gfc_router_create(const int *devices, int ndevices, size_t hbm_budget_bytes, int max_slots,
+                      gfc_router **out);
+
+/* As gfc_server_submit, on the least-loaded server (gfc_server_load; ties go
+ * to the lowest index). G_host is host memory, or device memory of the
+ * device that the chosen server runs on (GFC_EINVAL if it belongs to another
+ * device). The ticket names the server in its low 8 bits. */
+int gfc_router_submit(gfc_router *r, const gfc_propagator *prop, const gfc_params *params,
+                      const gfc_grid *grid, double *G_host, uint64_t *ticket);
+int gfc_router_poll(gfc_router *r, uint64_t ticket, int *done, int *status);
+int gfc_router_wait(gfc_router *r, uint64_t ticket, int timeout_ms);
+int gfc_router_cancel(gfc_router *r, uint64_t ticket);
+
+/* The index-th server (for gfc_server_stats, gfc_server_load), and the server
+ * index and server ticket that a router ticket names (for
+ * gfc_server_request_info). */
+int gfc_router_server(gfc_router *r, int index, gfc_server **out);
+int gfc_router_server_of(gfc_router *r, uint64_t ticket, int *index, uint64_t *server_ticket);
+
+/* Destroys every server (gfc_server_destroy) and the router. */
+int gfc_router_destroy(gfc_router *r);
 
 #ifdef __cplusplus
 }

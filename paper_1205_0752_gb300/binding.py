@@ -116,6 +116,20 @@ _SIGS = {
     "gfc_server_stats": ([_P, ctypes.POINTER(_ServerStats)], ctypes.c_int),
     "gfc_server_request_info": ([_P, ctypes.c_uint64, ctypes.POINTER(_RequestInfo)], ctypes.c_int),
     "gfc_server_destroy": ([_P], ctypes.c_int),
+    "gfc_server_load": ([_P, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+    "gfc_router_create": ([ctypes.POINTER(ctypes.c_int), ctypes.c_int, ctypes.c_size_t, ctypes.c_int,
+                           ctypes.POINTER(_P)], ctypes.c_int),
+    "gfc_router_submit": ([_P, ctypes.POINTER(_Prop), ctypes.POINTER(_Params),
+                           ctypes.POINTER(_Grid), _P, ctypes.POINTER(ctypes.c_uint64)],
+                          ctypes.c_int),
+    "gfc_router_poll": ([_P, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int),
+                         ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
+    "gfc_router_wait": ([_P, ctypes.c_uint64, ctypes.c_int], ctypes.c_int),
+    "gfc_router_cancel": ([_P, ctypes.c_uint64], ctypes.c_int),
+    "gfc_router_server": ([_P, ctypes.c_int, ctypes.POINTER(_P)], ctypes.c_int),
+    "gfc_router_server_of": ([_P, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int),
+                              ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
+    "gfc_router_destroy": ([_P], ctypes.c_int),
     "gfc_angular_map": ([ctypes.POINTER(_Prop), ctypes.POINTER(_Params), ctypes.c_double,
                          ctypes.c_double, _P, ctypes.c_int64, _P, _P], ctypes.c_int),
     "gfc_region_map": ([ctypes.POINTER(_Prop), _P, ctypes.c_int64, _P, _P], ctypes.c_int),
@@ -419,11 +433,94 @@ class Server:
                "gfc_server_request_info")
         return {k: getattr(r, k) for k, _ in _RequestInfo._fields_}
 
+    def load(self) -> float:
+        """Estimated work not yet launched (gfc_server_load)."""
+        w = ctypes.c_double()
+        _check(self._lib.gfc_server_load(self._h, ctypes.byref(w)), "gfc_server_load")
+        return w.value
+
     def close(self):
         if self._h:
             _check(self._lib.gfc_server_destroy(self._h), "gfc_server_destroy")
             self._h = None
             self._keep.clear()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+class _RouterServer(Server):
+    """A server owned by a router (destroyed with it)."""
+
+    def __init__(self, lib, handle):
+        self._lib = lib
+        self._h = handle
+        self._keep = {}
+
+    def close(self):
+        self._h = None
+
+
+class Router:
+    """One server per listed device, each request to the least-loaded one
+    (gfc_router_*)."""
+
+    def __init__(self, devices, hbm_budget_bytes: int = 40 << 30, max_slots: int = 64):
+        self._lib = load_library()
+        devs = (ctypes.c_int * len(devices))(*devices)
+        h = ctypes.c_void_p()
+        _check(self._lib.gfc_router_create(devs, len(devices), hbm_budget_bytes, max_slots,
+                                           ctypes.byref(h)), "gfc_router_create")
+        self._h = h
+        self._keep = {}
+        self.servers = []
+        for i in range(len(devices)):
+            sh = ctypes.c_void_p()
+            _check(self._lib.gfc_router_server(self._h, i, ctypes.byref(sh)), "gfc_router_server")
+            self.servers.append(_RouterServer(self._lib, sh))
+
+    def submit(self, prop, params, grid, out=None):
+        """As Server.submit, on the least-loaded server; returns (ticket, output)."""
+        import numpy as np
+        g = grid if isinstance(grid, _Grid) else make_grid(*grid)
+        G = out if out is not None else np.empty((g.m, g.n), dtype=np.complex128)
+        ptr = G.ctypes.data if isinstance(G, np.ndarray) else G.data_ptr()
+        t = ctypes.c_uint64()
+        _check(self._lib.gfc_router_submit(self._h, ctypes.byref(make_prop(prop)),
+                                           ctypes.byref(make_params(params)), ctypes.byref(g),
+                                           ctypes.c_void_p(ptr), ctypes.byref(t)),
+               "gfc_router_submit")
+        self._keep[t.value] = G
+        return t.value, G
+
+    def wait(self, ticket, timeout_ms: int = -1) -> int:
+        return self._lib.gfc_router_wait(self._h, ticket, int(timeout_ms))
+
+    def poll(self, ticket):
+        done, st = ctypes.c_int(), ctypes.c_int()
+        _check(self._lib.gfc_router_poll(self._h, ticket, ctypes.byref(done), ctypes.byref(st)),
+               "gfc_router_poll")
+        return bool(done.value), st.value
+
+    def cancel(self, ticket) -> int:
+        return self._lib.gfc_router_cancel(self._h, ticket)
+
+    def server_of(self, ticket):
+        """(server index, server ticket) of a router ticket."""
+        i, t = ctypes.c_int(), ctypes.c_uint64()
+        _check(self._lib.gfc_router_server_of(self._h, ticket, ctypes.byref(i), ctypes.byref(t)),
+               "gfc_router_server_of")
+        return i.value, t.value
+
+    def close(self):
+        if self._h:
+            _check(self._lib.gfc_router_destroy(self._h), "gfc_router_destroy")
+            self._h = None
+            self._keep.clear()
+            self.servers = []
 
     def __enter__(self):
         return self

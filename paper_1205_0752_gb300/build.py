@@ -13,8 +13,8 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libgfc.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["gfc_kernels.cu", "gfc_capi.cpp", "gfc_server.cpp", "gfc_noalloc.cu", "gfc_diag.cu",
-           "gfc_probe.cu"]
+SOURCES = ["gfc_kernels.cu", "gfc_capi.cpp", "gfc_server.cpp", "gfc_router.cpp", "gfc_noalloc.cu",
+           "gfc_diag.cu", "gfc_probe.cu"]
 # gfc_eval_inst.cu is compiled once per (arithmetic, unrolled angular pair
 # count) so that the kernel instantiations build in parallel; double-float
 # has the generic loop only

@@ -842,6 +842,17 @@ int gfc_server_stats(gfc_server *s, gfc_stats *out)
     return GFC_OK;
 }
 
+int gfc_server_load(gfc_server *s, double *work)
+{
+    if (!s || !work) return fail(GFC_EINVAL, "NULL argument");
+    std::lock_guard<std::mutex> lk(s->mu);
+    double w = 0.0;
+    for (const Request *r : s->queue) w += r->work_left;
+    for (const Request *r : s->active) w += r->work_left;
+    *work = w;
+    return GFC_OK;
+}
+
 int gfc_server_destroy(gfc_server *s)
 {
     if (!s) return fail(GFC_EINVAL, "NULL server");

@@ -30,7 +30,7 @@ def test_every_declared_function_is_exported():
 
 
 def test_version_and_strings():
-    assert gfc.version() == (1, 5)
+    assert gfc.version() == (1, 6)
     lib = gfc.load_library()
     assert lib.gfc_strerror(0) == b"ok"
     assert lib.gfc_strerror(-3) == b"request exceeds the memory budget"
@@ -93,3 +93,13 @@ def test_server_arguments_checked_on_the_host():
     assert lib.gfc_server_create(0, 1 << 30, 0, ctypes.byref(h)) == -1
     assert lib.gfc_server_create(0, 1 << 10, 4, ctypes.byref(h)) == -1
     assert lib.gfc_server_destroy(None) == -1
+
+
+def test_router_rejects_bad_arguments_on_the_host():
+    lib = gfc.load_library()
+    h = ctypes.c_void_p()
+    devs = (ctypes.c_int * 1)(0)
+    assert lib.gfc_router_create(devs, 0, 1 << 30, 8, ctypes.byref(h)) == -1
+    assert lib.gfc_router_create(devs, 257, 1 << 30, 8, ctypes.byref(h)) == -1
+    assert lib.gfc_router_create(None, 1, 1 << 30, 8, ctypes.byref(h)) == -1
+    assert lib.gfc_router_destroy(None) == -1
